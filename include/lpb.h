@@ -1,0 +1,179 @@
+/*
+ * lpb.h -- C ABI of liblpb, a batched linear-program solver for one GB300 GPU.
+ *
+ * Problem (Section 3, Eq. 1-3 of Gurung & Ray, "Solving Batched Linear Programs
+ * on GPU and Multicore CPU"): for every LP k of a batch
+ *
+ *     maximize  c^T x   subject to  A x <= b,  x >= 0,         A is m_k x n_k,
+ *
+ * and, as a closed-form special case (Section 6, Eq. 8), the support function
+ * of a hyperbox, maximize c^T x subject to l <= x <= u.
+ *
+ * Conventions shared by every call:
+ *   - Pointers documented as "device" point to memory of the handle's GPU and
+ *     are owned by the caller; the library never frees or keeps them past the
+ *     call.  Calls are asynchronous on `stream` (a cudaStream_t, NULL = the
+ *     legacy default stream) and return before the GPU work finishes.
+ *   - The library allocates device memory only in lpb_create (a few bytes of
+ *     counters and an error word).  All scratch comes from the caller's
+ *     workspace `ws` of at least lpb_workspace_size() bytes, 256-byte aligned.
+ *   - The return value (lpb_err) reports host-side validation and CUDA launch
+ *     errors only.  Mathematical outcomes (optimal, infeasible, unbounded, ...)
+ *     are per-LP lpb_status values written to result->status and are never an
+ *     error.  Faults detected inside kernels (a size outside the declared
+ *     bounds, an exhausted workspace) are recorded in the handle's device
+ *     error word and reported by lpb_sync_error(), which synchronises.
+ *   - No call traps, asserts or spins without bound on the device.
+ */
+#ifndef LPB_H_
+#define LPB_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Per-LP outcome (Section 3.1: the halt conditions "optimal" and "unbounded";
+ * Section 3: the auxiliary-LP optimum is non-zero -> "infeasible"). */
+typedef enum {
+  LPB_OPTIMAL = 0,
+  LPB_INFEASIBLE = 1,
+  LPB_UNBOUNDED = 2,
+  LPB_ITER_LIMIT = 3,   /* the pivot cap was reached */
+  LPB_NUMERIC = 4,      /* NaN/Inf in the data, or a numerical breakdown */
+  LPB_BAD_SIZE = 5      /* m or n outside 1..max_m / 1..max_n */
+} lpb_status;
+
+/* Per-call error codes. */
+typedef enum {
+  LPB_OK = 0,
+  LPB_EINVAL = -1,        /* a NULL pointer, a negative count, bad options */
+  LPB_ENOMEM = -2,        /* workspace smaller than lpb_workspace_size() */
+  LPB_ECUDA = -3,         /* a CUDA runtime call failed */
+  LPB_EUNSUPPORTED = -4,  /* a size or mode this build does not handle */
+  LPB_EDEVICE = -5        /* a kernel recorded a fault in the device error word */
+} lpb_err;
+
+/* Arithmetic of the simplex tableau. */
+typedef enum {
+  LPB_FP64 = 0,         /* FP64 tableau throughout */
+  LPB_FP32_REFINE = 1,  /* FP32 tableau; FP64 refinement, verification and FP64 re-solve */
+  LPB_FP32 = 2          /* FP32 tableau, results converted to FP64 unrefined */
+} lpb_precision;
+
+typedef enum { LPB_DTYPE_F32 = 0, LPB_DTYPE_F64 = 1 } lpb_dtype;
+
+/* A packed batch.  LP k has m[k] rows and n[k] structural variables; its
+ * A is m[k] x n[k] row-major at element offset a_off[k] of A, its b has m[k]
+ * elements at b_off[k] of b, its c has n[k] elements at c_off[k] of c.
+ * m, n, a_off, b_off, c_off, A, b, c are device pointers.  max_m and max_n are
+ * HOST values bounding every m[k] and n[k]; LPs outside them get LPB_BAD_SIZE.
+ * dtype (lpb_dtype) applies to A, b and c. */
+typedef struct {
+  int32_t count;
+  int32_t max_m, max_n;
+  int32_t dtype;
+  const int32_t *m, *n;
+  const int64_t *a_off, *b_off, *c_off;
+  const void *A, *b, *c;
+} lpb_batch;
+
+/* Caller-owned device outputs, FP64 whatever the input dtype.  status, iters
+ * and obj have `count` entries; x is packed like c (n[k] values at c_off[k]);
+ * y (the duals of A x <= b) and basis are packed like b (m[k] values at
+ * b_off[k]).  basis[i] is the variable basic in row i: 0..n-1 structural,
+ * n+j slack of row j, -1 for a redundant row.  Any of iters, y, basis may be
+ * NULL.  For a non-optimal LP x and y are 0 and obj is -inf (infeasible),
+ * +inf (unbounded) or NaN. */
+typedef struct {
+  int32_t *status;
+  int32_t *iters;
+  double *obj;
+  double *x;
+  double *y;
+  int32_t *basis;
+} lpb_result;
+
+/* Solver options; zero-initialised fields take the defaults in brackets. */
+typedef struct {
+  int32_t prec;              /* lpb_precision [LPB_FP64] */
+  int32_t max_iter;          /* pivot cap per LP [50 (m + n)] */
+  double eps_p;              /* Step 2 eligibility t_ie > eps_p [1e-9 FP64, 1e-6 FP32] */
+  double eps_d;              /* Step 1 eligibility r_j < -eps_d [1e-9 FP64, 1e-6 FP32] */
+  double feas_tol;           /* Phase I / verification tolerance [1e-9] */
+  int32_t keep_basis_inverse;/* keep what lpb_solve_backward needs in ws [0] */
+  int32_t kernel;            /* lpb_kernel: force a kernel class [LPB_KERNEL_AUTO] */
+  int32_t threads;           /* threads per CTA for the tableau kernel, 0 = auto */
+  int32_t reserved;
+} lpb_options;
+
+typedef enum {
+  LPB_KERNEL_AUTO = 0,
+  LPB_KERNEL_SMEM = 1,   /* tableau in shared memory, one CTA per LP */
+  LPB_KERNEL_GMEM = 2,   /* tableau in a per-CTA workspace slot (L2 resident) */
+  LPB_KERNEL_REG = 3     /* tableau in registers (FP32, m < 128, type 1) */
+} lpb_kernel;
+
+typedef struct lpb_handle lpb_handle;
+
+/* Create a handle bound to CUDA device `device`; allocates its counters. */
+lpb_err lpb_create(lpb_handle **handle, int device);
+/* Free the handle (synchronises the device first). */
+lpb_err lpb_destroy(lpb_handle *handle);
+
+/* Workspace bytes lpb_solve / lpb_solve_backward need for this batch shape
+ * and these options (depends only on count, max_m, max_n, dtype, options). */
+lpb_err lpb_workspace_size(lpb_handle *handle, const lpb_batch *batch, const lpb_options *opt,
+                           size_t *bytes);
+
+/* Solve every LP of the batch (Section 3.1 Steps 1-3 with Dantzig's rule,
+ * Phase I of Section 3 when some b_i < 0).  Asynchronous on `stream`. */
+lpb_err lpb_solve(lpb_handle *handle, const lpb_batch *batch, const lpb_options *opt,
+                  const lpb_result *result, void *ws, size_t ws_bytes, void *stream);
+
+/* Vector-Jacobian product of obj and x* through the optimal basis of a
+ * previous lpb_solve of the same batch with the same ws (which must have run
+ * with keep_basis_inverse = 1, or the basis is refactorised).  g_obj [count]
+ * and g_x (packed like c) are the upstream gradients (either may be NULL = 0).
+ * Writes g_c (like c), g_b (like b), g_A (like A), all FP64 device arrays:
+ *   d obj/dc = x*,  d obj/db = y,  d obj/dA = -y x*^T,
+ *   for x*: v = B^{-T} g_B,  d/db += v,  d/dA += -v x*^T,  d/dc += 0.
+ * Non-optimal LPs get zero gradients. */
+lpb_err lpb_solve_backward(lpb_handle *handle, const lpb_batch *batch, const lpb_options *opt,
+                           const lpb_result *result, const double *g_obj, const double *g_x,
+                           double *g_c, double *g_b, double *g_A, void *ws, size_t ws_bytes,
+                           void *stream);
+
+/* Hyperbox support functions, Section 6 Eq. 8: for k < count,
+ * obj[k] = sum_i c[k][i] * h_i with h_i = l_i if c[k][i] < 0 else u_i, summed
+ * in index order from +0.0 with each product rounded (no FMA).
+ * c is count x n row-major; l and u are count x n (shared_box = 0) or n values
+ * (shared_box = 1); obj has count values; x (nullable) receives h, count x n.
+ * All arrays have dtype `dtype` and live on the device. */
+lpb_err lpb_hyperbox(lpb_handle *handle, int64_t count, int32_t n, int32_t dtype,
+                     const void *c, const void *l, const void *u, int32_t shared_box,
+                     void *obj, void *x, void *stream);
+
+/* Synchronise `stream`, read and clear the device error word.  Returns
+ * LPB_OK or LPB_EDEVICE (word != 0; *word receives it when non-NULL). */
+lpb_err lpb_sync_error(lpb_handle *handle, void *stream, uint32_t *word);
+
+/* Counters of the last lpb_solve (synchronises `stream`): LPs re-solved in
+ * FP64 after failing FP32 verification, and LPs deferred from the register
+ * kernel to the shared-memory kernel. */
+typedef struct {
+  int64_t resolved_fp64;
+  int64_t deferred;
+  int64_t reserved[6];
+} lpb_stats;
+lpb_err lpb_get_stats(lpb_handle *handle, void *stream, lpb_stats *stats);
+
+const char *lpb_strerror(lpb_err err);
+const char *lpb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LPB_H_ */
