@@ -170,6 +170,15 @@ typedef struct {
 } lpb_stats;
 lpb_err lpb_get_stats(lpb_handle *handle, void *stream, lpb_stats *stats);
 
+/* Kernel timing.  lpb_profile_start(h, calls) makes the next `calls` (<= 256)
+ * lpb_solve calls record a CUDA event pair on their stream around each of
+ * their kernel passes (pass 0: every LP; pass 1: LPs needing more artificial
+ * columns; pass 2: the FP64 re-solve).  lpb_profile_read synchronises those
+ * events, writes ms[3 * i + p] = milliseconds of pass p in recorded call i
+ * (0 when the pass did not launch), sets *ncalls and stops recording. */
+lpb_err lpb_profile_start(lpb_handle *handle, int32_t calls);
+lpb_err lpb_profile_read(lpb_handle *handle, float *ms, int32_t max_calls, int32_t *ncalls);
+
 const char *lpb_strerror(lpb_err err);
 const char *lpb_version(void);
 

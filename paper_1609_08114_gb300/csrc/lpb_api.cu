@@ -1,0 +1,375 @@
+// lpb_api.cu -- the C ABI of liblpb (declared in include/lpb.h).
+//
+// Host side only: argument validation, the pass plan of a solve, workspace
+// carving and kernel launches.  Every pass is a fixed-size persistent launch
+// whose work list length lives on the device, so a whole lpb_solve is a
+// static sequence of memset + kernels with no host synchronisation (it can be
+// captured in a CUDA graph).
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "lpb_internal.cuh"
+
+struct lpb_handle {
+  int device;
+  int sms;
+  size_t smem_optin;
+  size_t l2_bytes;
+  uint32_t *d_err;
+  int32_t *d_ctr;   // work queues and list lengths, zeroed by every lpb_solve
+  // Kernel timing (lpb_profile_*): one event pair per pass per recorded call.
+  static constexpr int kProfMax = 256;
+  cudaEvent_t *prof_ev = nullptr;   // [kProfMax * 3 * 2]
+  bool prof_ran[kProfMax * 3] = {};
+  int prof_cap = 0, prof_n = 0;
+};
+
+namespace {
+
+using namespace lpb;
+
+enum { CTR_Q1 = 0, CTR_Q2 = 1, CTR_Q3 = 2, CTR_DEFER = 4, CTR_RESOLVE = 5, CTR_N = 8 };
+
+class DeviceScope {
+ public:
+  explicit DeviceScope(int dev) {
+    cudaGetDevice(&prev_);
+    ok_ = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceScope() { cudaSetDevice(prev_); }
+  bool ok() const { return ok_; }
+
+ private:
+  int prev_ = 0;
+  bool ok_ = false;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Pass {
+  bool fp64 = false, gmem = false;
+  int kcap = 0, mode = MODE_FP64, grid = 0, threads = 128;
+  size_t smem = 0, slot_bytes = 0;
+};
+
+struct Plan {
+  Pass pass[3];
+  int npass = 0;
+  bool resolve = false;      // pass 2 (index 2) re-solves FP32 failures in FP64
+  bool own_basis = false;    // basis lives in the workspace
+  size_t off_defer = 0, off_resolve = 0, off_basis = 0, off_slots = 0, total = 0;
+  double eps_p = 0, eps_d = 0, feas_tol = 0;
+};
+
+int auto_threads(int max_m, int max_n) {
+  int t = (max_m > max_n ? max_m : max_n);
+  t = (t + 31) & ~31;
+  if (t < 64) t = 64;
+  if (t > 256) t = 256;
+  return t;
+}
+
+lpb_err make_pass(const lpb_handle *h, const lpb_batch *b, const lpb_options *o, bool fp64, int kcap,
+                  int mode, Pass *p) {
+  const int eb = fp64 ? 8 : 4;
+  const bool refine = (mode == MODE_FP32_REFINE) && !fp64;
+  p->fp64 = fp64;
+  p->kcap = kcap;
+  p->mode = mode;
+  p->threads = o->threads > 0 ? o->threads : auto_threads(b->max_m, b->max_n);
+  if (p->threads < 32 || p->threads > 512 || (p->threads & 31)) return LPB_EINVAL;
+  const size_t smem_s = tableau_smem_bytes(eb, false, b->max_m, b->max_n, kcap, p->threads, refine);
+  const bool want_gmem = o->kernel == LPB_KERNEL_GMEM || smem_s > h->smem_optin;
+  if (o->kernel == LPB_KERNEL_SMEM && smem_s > h->smem_optin) return LPB_EUNSUPPORTED;
+  int occ = 0;
+  if (!want_gmem) {
+    p->gmem = false;
+    p->smem = smem_s;
+    if (tableau_max_ctas_per_sm(eb, false, p->threads, p->smem, &occ) != cudaSuccess) return LPB_ECUDA;
+    if (occ < 1) return LPB_EUNSUPPORTED;
+    p->grid = occ * h->sms;
+  } else {
+    p->gmem = true;
+    p->smem = tableau_smem_bytes(eb, true, b->max_m, b->max_n, kcap, p->threads, refine);
+    if (p->smem > h->smem_optin) return LPB_EUNSUPPORTED;
+    p->slot_bytes = tableau_slot_bytes(eb, b->max_m, b->max_n, kcap);
+    if (tableau_max_ctas_per_sm(eb, true, p->threads, p->smem, &occ) != cudaSuccess) return LPB_ECUDA;
+    if (occ < 1) return LPB_EUNSUPPORTED;
+    // Keep the in-flight tableaux within about 3/4 of L2, but use every SM.
+    size_t fit = (h->l2_bytes * 3 / 4) / p->slot_bytes;
+    if (fit < size_t(h->sms)) fit = size_t(h->sms);
+    p->grid = int(fit < size_t(occ) * h->sms ? fit : size_t(occ) * h->sms);
+  }
+  if (p->grid > b->count) p->grid = b->count > 0 ? b->count : 1;
+  return LPB_OK;
+}
+
+lpb_err make_plan(const lpb_handle *h, const lpb_batch *b, const lpb_options *o, bool basis_given,
+                  Plan *pl) {
+  if (!h || !b || !o) return LPB_EINVAL;
+  if (b->count < 0) return LPB_EINVAL;
+  if (b->max_m < 1 || b->max_n < 1 || b->max_m > kMaxDim || b->max_n > kMaxDim) return LPB_EUNSUPPORTED;
+  if (b->dtype != LPB_DTYPE_F32 && b->dtype != LPB_DTYPE_F64) return LPB_EINVAL;
+  if (o->prec < LPB_FP64 || o->prec > LPB_FP32) return LPB_EINVAL;
+  if (o->max_iter < 0 || o->eps_p < 0 || o->eps_d < 0 || o->feas_tol < 0) return LPB_EINVAL;
+  const bool fp32 = o->prec != LPB_FP64;
+  pl->eps_p = o->eps_p > 0 ? o->eps_p : (fp32 ? 1e-6 : 1e-9);
+  pl->eps_d = o->eps_d > 0 ? o->eps_d : (fp32 ? 1e-6 : 1e-9);
+  pl->feas_tol = o->feas_tol > 0 ? o->feas_tol : 1e-9;
+  lpb_err e;
+  const int mode = o->prec == LPB_FP64 ? MODE_FP64 : o->prec == LPB_FP32 ? MODE_FP32 : MODE_FP32_REFINE;
+  if ((e = make_pass(h, b, o, !fp32, 0, mode, &pl->pass[0])) != LPB_OK) return e;
+  if ((e = make_pass(h, b, o, !fp32, b->max_m, mode, &pl->pass[1])) != LPB_OK) return e;
+  pl->npass = 2;
+  pl->resolve = o->prec == LPB_FP32_REFINE;
+  if (pl->resolve) {
+    lpb_options o64 = *o;
+    if (o64.kernel == LPB_KERNEL_REG) o64.kernel = LPB_KERNEL_AUTO;
+    if ((e = make_pass(h, b, &o64, true, b->max_m, MODE_FP64, &pl->pass[2])) != LPB_OK) return e;
+    pl->npass = 3;
+  }
+  pl->own_basis = pl->resolve && !basis_given;
+  size_t off = 0;
+  const size_t cnt = size_t(b->count > 0 ? b->count : 1);
+  pl->off_defer = off;   off = align256(off + cnt * 4);
+  pl->off_resolve = off; off = align256(off + cnt * 4);
+  pl->off_basis = off;   off = align256(off + (pl->own_basis ? cnt * size_t(b->max_m) * 4 : 0));
+  pl->off_slots = off;
+  size_t slots = 0;
+  for (int i = 0; i < pl->npass; ++i)
+    if (pl->pass[i].gmem) {
+      const size_t s = size_t(pl->pass[i].grid) * pl->pass[i].slot_bytes;
+      if (s > slots) slots = s;
+    }
+  pl->total = align256(off + slots);
+  return LPB_OK;
+}
+
+TableauParams base_params(const lpb_handle *h, const lpb_batch *b, const lpb_result *r,
+                          const lpb_options *o, const Plan &pl, unsigned char *ws) {
+  TableauParams p{};
+  p.B = BatchDev{b->count, b->max_m, b->max_n, b->dtype, b->m, b->n, b->a_off, b->b_off, b->c_off,
+                 b->A, b->b, b->c};
+  p.R = ResultDev{r->status, r->iters, r->obj, r->x, r->y, r->basis};
+  p.defer_items = reinterpret_cast<int32_t *>(ws + pl.off_defer);
+  p.defer_count = h->d_ctr + CTR_DEFER;
+  p.resolve_items = reinterpret_cast<int32_t *>(ws + pl.off_resolve);
+  p.resolve_count = h->d_ctr + CTR_RESOLVE;
+  p.list_cap = b->count;
+  p.bbuf = pl.own_basis ? reinterpret_cast<int32_t *>(ws + pl.off_basis) : r->basis;
+  p.bpacked = pl.own_basis ? 0 : 1;
+  p.slots = ws + pl.off_slots;
+  p.max_iter = o->max_iter;
+  p.eps_p = pl.eps_p;
+  p.eps_d = pl.eps_d;
+  p.feas_tol = pl.feas_tol;
+  p.err = h->d_err;
+  return p;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lpb_version(void) { return "liblpb 0.1 (sm_103a)"; }
+
+const char *lpb_strerror(lpb_err err) {
+  switch (err) {
+    case LPB_OK: return "ok";
+    case LPB_EINVAL: return "invalid argument";
+    case LPB_ENOMEM: return "workspace too small";
+    case LPB_ECUDA: return "CUDA runtime error";
+    case LPB_EUNSUPPORTED: return "unsupported size or mode";
+    case LPB_EDEVICE: return "a kernel recorded a device-side fault";
+  }
+  return "unknown error";
+}
+
+lpb_err lpb_create(lpb_handle **handle, int device) {
+  if (!handle) return LPB_EINVAL;
+  *handle = nullptr;
+  DeviceScope ds(device);
+  if (!ds.ok()) return LPB_ECUDA;
+  lpb_handle *h = new (std::nothrow) lpb_handle{};
+  if (!h) return LPB_ENOMEM;
+  h->device = device;
+  int v = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  h->smem_optin = size_t(v);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, device);
+  h->l2_bytes = size_t(v);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_err, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_ctr, CTR_N * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(h->d_ctr, 0, CTR_N * sizeof(int32_t));
+  if (e != cudaSuccess) {
+    cudaFree(h->d_err);
+    cudaFree(h->d_ctr);
+    delete h;
+    return LPB_ECUDA;
+  }
+  *handle = h;
+  return LPB_OK;
+}
+
+lpb_err lpb_destroy(lpb_handle *h) {
+  if (!h) return LPB_EINVAL;
+  {
+    DeviceScope ds(h->device);
+    cudaDeviceSynchronize();
+    cudaFree(h->d_err);
+    cudaFree(h->d_ctr);
+    if (h->prof_ev) {
+      for (int i = 0; i < lpb_handle::kProfMax * 3 * 2; ++i) cudaEventDestroy(h->prof_ev[i]);
+      delete[] h->prof_ev;
+    }
+  }
+  delete h;
+  return LPB_OK;
+}
+
+lpb_err lpb_workspace_size(lpb_handle *h, const lpb_batch *b, const lpb_options *o, size_t *bytes) {
+  if (!h || !b || !o || !bytes) return LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  Plan pl;
+  // Size for the worst case: the basis may have to live in the workspace.
+  const lpb_err e = make_plan(h, b, o, false, &pl);
+  if (e != LPB_OK) return e;
+  *bytes = pl.total;
+  return LPB_OK;
+}
+
+lpb_err lpb_solve(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const lpb_result *r,
+                  void *ws, size_t ws_bytes, void *stream) {
+  if (!h || !b || !o || !r) return LPB_EINVAL;
+  if (b->count < 0) return LPB_EINVAL;
+  if (b->count == 0) return LPB_OK;
+  if (!b->m || !b->n || !b->a_off || !b->b_off || !b->c_off || !b->A || !b->b || !b->c) return LPB_EINVAL;
+  if (!r->status || !r->obj || !r->x) return LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  Plan pl;
+  lpb_err e = make_plan(h, b, o, r->basis != nullptr, &pl);
+  if (e != LPB_OK) return e;
+  if (ws_bytes < pl.total || (pl.total > 0 && !ws)) return LPB_ENOMEM;
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return LPB_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char *w = static_cast<unsigned char *>(ws);
+  if (cudaMemsetAsync(h->d_ctr, 0, CTR_N * sizeof(int32_t), s) != cudaSuccess) return LPB_ECUDA;
+  const bool prof = h->prof_ev && h->prof_n < h->prof_cap;
+  for (int i = 0; i < pl.npass; ++i) {
+    const Pass &ps = pl.pass[i];
+    cudaEvent_t *ev = prof ? h->prof_ev + (size_t(h->prof_n) * 3 + i) * 2 : nullptr;
+    if (ev && cudaEventRecord(ev[0], s) != cudaSuccess) return LPB_ECUDA;
+    TableauParams p = base_params(h, b, r, o, pl, w);
+    p.kcap = ps.kcap;
+    p.mode = ps.mode;
+    p.slot_bytes = ps.slot_bytes;
+    p.queue = h->d_ctr + (i == 0 ? CTR_Q1 : i == 1 ? CTR_Q2 : CTR_Q3);
+    if (i == 0) {
+      p.in = WorkList{nullptr, nullptr};
+    } else if (i == 1) {
+      p.in = WorkList{p.defer_items, p.defer_count};
+      p.defer_items = nullptr;   // kcap = max_m: nothing is deferred again
+    } else {
+      p.in = WorkList{p.resolve_items, p.resolve_count};
+      p.warm = 1;
+    }
+    if (launch_tableau(p, ps.fp64, ps.gmem, ps.grid, ps.threads, ps.smem, s) != cudaSuccess) return LPB_ECUDA;
+    if (ev) {
+      if (cudaEventRecord(ev[1], s) != cudaSuccess) return LPB_ECUDA;
+      h->prof_ran[h->prof_n * 3 + i] = true;
+    }
+  }
+  if (prof) ++h->prof_n;
+  return LPB_OK;
+}
+
+lpb_err lpb_profile_start(lpb_handle *h, int32_t calls) {
+  if (!h || calls < 1 || calls > lpb_handle::kProfMax) return LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  if (!h->prof_ev) {
+    h->prof_ev = new (std::nothrow) cudaEvent_t[lpb_handle::kProfMax * 3 * 2];
+    if (!h->prof_ev) return LPB_ENOMEM;
+    for (int i = 0; i < lpb_handle::kProfMax * 3 * 2; ++i)
+      if (cudaEventCreate(&h->prof_ev[i]) != cudaSuccess) return LPB_ECUDA;
+  }
+  std::memset(h->prof_ran, 0, sizeof(h->prof_ran));
+  h->prof_cap = calls;
+  h->prof_n = 0;
+  return LPB_OK;
+}
+
+lpb_err lpb_profile_read(lpb_handle *h, float *ms, int32_t max_calls, int32_t *ncalls) {
+  if (!h || !ms || !ncalls || max_calls < 0) return LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  const int n = h->prof_n < max_calls ? h->prof_n : max_calls;
+  for (int i = 0; i < n; ++i)
+    for (int p = 0; p < 3; ++p) {
+      ms[3 * i + p] = 0.f;
+      if (!h->prof_ran[i * 3 + p]) continue;
+      cudaEvent_t *ev = h->prof_ev + (size_t(i) * 3 + p) * 2;
+      if (cudaEventSynchronize(ev[1]) != cudaSuccess) return LPB_ECUDA;
+      if (cudaEventElapsedTime(&ms[3 * i + p], ev[0], ev[1]) != cudaSuccess) return LPB_ECUDA;
+    }
+  *ncalls = n;
+  h->prof_cap = 0;
+  h->prof_n = 0;
+  return LPB_OK;
+}
+
+lpb_err lpb_solve_backward(lpb_handle *h, const lpb_batch *b, const lpb_options *o,
+                           const lpb_result *r, const double *g_obj, const double *g_x, double *g_c,
+                           double *g_b, double *g_A, void *ws, size_t ws_bytes, void *stream) {
+  (void)h; (void)b; (void)o; (void)r; (void)g_obj; (void)g_x; (void)g_c; (void)g_b; (void)g_A;
+  (void)ws; (void)ws_bytes; (void)stream;
+  return LPB_EUNSUPPORTED;
+}
+
+lpb_err lpb_hyperbox(lpb_handle *h, int64_t count, int32_t n, int32_t dtype, const void *c,
+                     const void *l, const void *u, int32_t shared_box, void *obj, void *x,
+                     void *stream) {
+  if (!h || count < 0 || n < 1) return LPB_EINVAL;
+  if (dtype != LPB_DTYPE_F32 && dtype != LPB_DTYPE_F64) return LPB_EINVAL;
+  if (count == 0) return LPB_OK;
+  if (!c || !l || !u || !obj) return LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  const size_t smem = hyperbox_smem_bytes(n, dtype == LPB_DTYPE_F64 ? 8 : 4, shared_box != 0);
+  if (smem > h->smem_optin) return LPB_EUNSUPPORTED;
+  HyperboxParams p{count, n, dtype, shared_box != 0, c, l, u, obj, x};
+  return launch_hyperbox(p, static_cast<cudaStream_t>(stream)) == cudaSuccess ? LPB_OK : LPB_ECUDA;
+}
+
+lpb_err lpb_sync_error(lpb_handle *h, void *stream, uint32_t *word) {
+  if (!h) return LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  uint32_t v = 0;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return LPB_ECUDA;
+  if (cudaMemcpy(&v, h->d_err, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return LPB_ECUDA;
+  if (cudaMemset(h->d_err, 0, sizeof(v)) != cudaSuccess) return LPB_ECUDA;
+  if (word) *word = v;
+  return v ? LPB_EDEVICE : LPB_OK;
+}
+
+lpb_err lpb_get_stats(lpb_handle *h, void *stream, lpb_stats *st) {
+  if (!h || !st) return LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  int32_t c[CTR_N];
+  if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return LPB_ECUDA;
+  if (cudaMemcpy(c, h->d_ctr, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return LPB_ECUDA;
+  std::memset(st, 0, sizeof(*st));
+  st->deferred = c[CTR_DEFER];
+  st->resolved_fp64 = c[CTR_RESOLVE];
+  return LPB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// lpb_internal.cuh -- device-side types and helpers shared by the liblpb kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <climits>
+#include <cmath>
+
+#include "lpb.h"
+
+namespace lpb {
+
+constexpr unsigned kFull = 0xffffffffu;
+// Reduction keys pack (variable index << kIdxBits) | (row or column).  Rows and
+// columns stay below 2^13, variables below 3 * 2^13, so keys fit in 29 bits.
+constexpr int kIdxBits = 13;
+constexpr int kIdxMask = (1 << kIdxBits) - 1;
+constexpr int kMaxDim = 4096;           // largest m or n accepted by this build
+
+// Bits of the handle's device error word.
+enum : uint32_t {
+  ERR_LIST_OVERFLOW = 1u,   // a work list received more entries than it can hold
+  ERR_SLOT_OVERFLOW = 2u,   // an LP did not fit the tableau slot of its launch
+  ERR_BAD_LAUNCH = 4u,      // a kernel was launched with an inconsistent configuration
+};
+
+enum Mode : int { MODE_FP64 = 0, MODE_FP32_REFINE = 1, MODE_FP32 = 2 };
+constexpr int STATUS_PENDING = -1;      // internal: the LP waits for a later pass
+
+struct BatchDev {
+  int count, max_m, max_n, dtype;
+  const int32_t *m, *n;
+  const int64_t *a_off, *b_off, *c_off;
+  const void *A, *b, *c;
+};
+
+struct ResultDev {
+  int32_t *status, *iters;
+  double *obj, *x, *y;
+  int32_t *basis;
+};
+
+// A list of LP indices with a device-resident length.  `items == nullptr`
+// means the identity list 0..B.count-1.
+struct WorkList {
+  const int32_t *items;
+  const int32_t *count;
+};
+
+// Input element `i` of an array of dtype `dt`, widened to double.
+__device__ __forceinline__ double ld_in(const void *p, int64_t i, int dt) {
+  return dt == LPB_DTYPE_F64 ? __ldg(static_cast<const double *>(p) + i)
+                             : static_cast<double>(__ldg(static_cast<const float *>(p) + i));
+}
+
+// (value, key) order: smaller value first, then smaller key.
+template <typename T>
+__device__ __forceinline__ void keep_better(T &v, int &k, T ov, int ok) {
+  if (ov < v || (ov == v && ok < k)) { v = ov; k = ok; }
+}
+
+template <typename T>
+__device__ __forceinline__ void warp_argmin(T &v, int &k) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const T ov = __shfl_xor_sync(kFull, v, off);
+    const int ok = __shfl_xor_sync(kFull, k, off);
+    keep_better(v, k, ov, ok);
+  }
+}
+
+// Every thread of the block receives the block-wide minimum.  `bv`/`bk` hold
+// one slot per warp; a call site must not reuse them before the block has
+// passed another __syncthreads().
+template <typename T>
+__device__ __forceinline__ void block_argmin(T &v, int &k, T *bv, int *bk) {
+  warp_argmin(v, k);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) { bv[w] = v; bk[w] = k; }
+  __syncthreads();
+  v = bv[0];
+  k = bk[0];
+  for (int i = 1; i < nw; ++i) keep_better(v, k, bv[i], bk[i]);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+  return v;
+}
+
+// Append `lp` to a work list of capacity `cap`; flags an overflow instead of
+// writing out of bounds.
+__device__ __forceinline__ void list_push(int32_t *items, int32_t *count, int cap, int lp,
+                                          uint32_t *err) {
+  const int at = atomicAdd(count, 1);
+  if (at < cap) items[at] = lp;
+  else atomicOr(err, ERR_LIST_OVERFLOW);
+}
+
+// ---- launch parameters ----------------------------------------------------
+
+struct TableauParams {
+  BatchDev B;
+  ResultDev R;
+  WorkList in;                 // LPs this launch solves
+  int32_t *queue;              // work counter, zeroed before the launch
+  int32_t *defer_items, *defer_count;     // LPs needing more artificial columns than kcap
+  int32_t *resolve_items, *resolve_count; // LPs failing FP32 verification
+  int list_cap;                // capacity of the defer / resolve lists
+  int32_t *bbuf;               // basis output (and warm-start input): packed like b when
+  int bpacked;                 //   bpacked, else max_m entries per LP
+  int warm;                    // start from the basis in bbuf (FP64 re-solve)
+  void *slots;                 // GMEM class: per-CTA tableau slots
+  size_t slot_bytes;
+  int kcap;                    // artificial columns this launch can hold
+  int mode;                    // Mode
+  int max_iter;                // 0: 50 (m + n)
+  double eps_p, eps_d, feas_tol;
+  uint32_t *err;
+};
+
+struct HyperboxParams {
+  int64_t count;
+  int n, dtype, shared_box;
+  const void *c, *l, *u;
+  void *obj, *x;
+};
+
+// Launchers (simplex_tableau.cu, hyperbox.cu).
+size_t tableau_smem_bytes(int elem_bytes, bool gmem, int max_m, int max_n, int kcap, int threads,
+                          bool refine);
+size_t tableau_slot_bytes(int elem_bytes, int max_m, int max_n, int kcap);
+cudaError_t tableau_max_ctas_per_sm(int elem_bytes, bool gmem, int threads, size_t smem, int *ctas);
+cudaError_t launch_tableau(const TableauParams &p, bool fp64, bool gmem, int grid, int threads,
+                           size_t smem, cudaStream_t s);
+size_t hyperbox_smem_bytes(int n, int elem_bytes, bool shared_box);
+cudaError_t launch_hyperbox(const HyperboxParams &p, cudaStream_t s);
+
+}  // namespace lpb

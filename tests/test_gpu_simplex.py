@@ -1,0 +1,151 @@
+"""GPU parity of the batched simplex (liblpb.so through the C ABI) against the FP64 oracle.
+
+Statuses must match exactly; objectives within 1e-9 relative in FP64 and 1e-8 after
+FP32 + FP64 refinement; x* and y to 1e-7 where the oracle certifies the optimum unique;
+and the GPU's own (x, y) must satisfy KKT in FP64 on every optimal LP.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from lp_helpers import compare, host, to_device
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def solver():
+    from paper_1609_08114_gb300 import Solver
+    return Solver(0)
+
+
+def run(solver, sb, prec, dtype=torch.float64, **kw):
+    res = solver.solve(to_device(sb, dtype=dtype), prec=prec, **kw)
+    return host(res)
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-9), ("fp32_refine", 1e-8)])
+def test_type1_m16_full_batch(solver, prec, rtol):
+    """1,000 LPs of m = n = 16 (A ~ U[0.1,1], b ~ U[1,10], c ~ U[0,1], seed 0)."""
+    sb = synth.type1(1000, 16, 16, seed=0)
+    got = run(solver, sb, prec)
+    ref, n_unique = compare(sb, got, obj_rtol=rtol)
+    assert np.all(got["status"] == 0) and n_unique > 900
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-9), ("fp32_refine", 1e-8)])
+@pytest.mark.parametrize("kernel", [1, 2])   # shared-memory and L2-slot tableau classes
+def test_type1_m100_sample(solver, prec, rtol, kernel):
+    """300 LPs of the m = n = 100 workload, through both tableau classes."""
+    sb = synth.type1(50000, 100, 100, seed=1, first=1000, stop=1300)
+    got = run(solver, sb, prec, kernel=kernel)
+    compare(sb, got, obj_rtol=rtol)
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-9), ("fp32_refine", 1e-8)])
+def test_type2_two_phase(solver, prec, rtol):
+    """Infeasible initial basis: Phase I, with infeasible and unbounded LPs mixed in."""
+    sb = synth.type2(240, 48, 40, seed=2, frac_infeasible=0.1, frac_unbounded=0.1)
+    got = run(solver, sb, prec)
+    ref, _ = compare(sb, got, obj_rtol=rtol)
+    assert set(np.unique(ref["status"])) == {0, 1, 2}
+    assert np.all(np.isinf(got["obj"][got["status"] == 1]) & (got["obj"][got["status"] == 1] < 0))
+    assert np.all(np.isinf(got["obj"][got["status"] == 2]) & (got["obj"][got["status"] == 2] > 0))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine", "fp32"])
+def test_handworked_golden(solver, prec):
+    cases = json.load(open(os.path.join(HERE, "golden", "handworked_lps.json")))["cases"]
+    sb = synth.pack([(np.array(c["A"], float), np.array(c["b"], float), np.array(c["c"], float)) for c in cases])
+    got = run(solver, sb, prec)
+    for k, c in enumerate(cases):
+        assert got["status"][k] == c["status"], c["name"]
+        if c["status"] == 0:
+            assert abs(got["obj"][k] - c["obj"]) <= (1e-12 if prec != "fp32" else 1e-5) * (1 + abs(c["obj"])), c["name"]
+
+
+def _tiny_integer_lps(seed, count):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        m = int(rng.integers(1, 6)); n = int(rng.integers(1, 6))
+        out.append((rng.integers(-3, 4, size=(m, n)).astype(float), rng.integers(-3, 6, size=m).astype(float),
+                    rng.integers(-2, 4, size=n).astype(float)))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+def test_tiny_degenerate_lps_all_statuses(solver, prec):
+    """Integer data: ties, degenerate vertices, redundant rows, all three statuses."""
+    sb = synth.pack(_tiny_integer_lps(5, 600))
+    got = run(solver, sb, prec)
+    ref, _ = compare(sb, got, obj_rtol=1e-9, check_unique=False)
+    assert set(np.unique(ref["status"])) == {0, 1, 2}
+
+
+def test_mixed_sizes_small(solver):
+    sb = synth.mixed_sizes(120, seed=4, lo=1, hi=64)
+    for prec in ("fp64", "fp32_refine"):
+        got = run(solver, sb, prec)
+        compare(sb, got, obj_rtol=1e-9 if prec == "fp64" else 1e-8)
+
+
+def test_fp32_input_dtype(solver):
+    sb = synth.type1(200, 30, 20, seed=8)
+    got = run(solver, sb, "fp32_refine", dtype=torch.float32)
+    sb32 = synth.pack([tuple(a.astype(np.float32).astype(np.float64) for a in sb.lp(k)) for k in range(sb.count)])
+    compare(sb32, got, obj_rtol=1e-8)
+
+
+def test_edge_cases(solver):
+    from paper_1609_08114_gb300 import LPBatch
+    # empty batch
+    empty = synth.pack([])
+    lb = LPBatch.from_packed(empty.m, empty.n, empty.A, empty.b, empty.c, device="cuda", max_m=4, max_n=4)
+    r = solver.solve(lb, prec="fp64")
+    assert r.status.numel() == 0
+    # m = 1 / n = 1 and a size above the declared bound
+    lps = [(np.array([[2.0]]), np.array([7.0]), np.array([3.0])),
+           (np.ones((1, 9)), np.array([4.0]), np.arange(9.0)),
+           (np.ones((9, 1)), np.arange(1.0, 10.0), np.array([1.0]))]
+    sb = synth.pack(lps)
+    got = host(solver.solve(to_device(sb, max_m=9, max_n=9), prec="fp64"))
+    compare(sb, got)
+    big = synth.pack(lps + [(np.ones((12, 3)), np.ones(12), np.ones(3))])
+    got = host(solver.solve(to_device(big, max_m=9, max_n=9), prec="fp64"))
+    assert list(got["status"]) == [0, 0, 0, 5]
+    # NaN in the data -> numeric status, others unaffected
+    A, b, c = lps[1]
+    A = A.copy(); A[0, 3] = np.nan
+    got = host(solver.solve(to_device(synth.pack([lps[0], (A, b, c), lps[2]])), prec="fp64"))
+    assert list(got["status"]) == [0, 4, 0]
+    # iteration cap
+    sb = synth.type1(4, 30, 30, seed=9)
+    got = host(solver.solve(to_device(sb), prec="fp64", max_iter=2))
+    assert np.all(got["status"] == 3) and np.all(got["iters"] == 2)
+    assert solver.sync_error() == 0
+
+
+def test_full_size_sampled_parity(solver):
+    """The 50,000 x (m = n = 100) batch in the benchmark's launch configuration; the oracle
+    checks a sample of 400 LPs spread over the batch."""
+    sb = synth.type1(50000, 100, 100, seed=1)
+    dev = to_device(sb)
+    idx = np.unique(np.linspace(0, 49999, 400).astype(int))
+    for prec, rtol in (("fp32_refine", 1e-8), ("fp64", 1e-9)):
+        got = host(solver.solve(dev, prec=prec))
+        assert np.all(got["status"] == 0)
+        sub = sb.subset(idx)
+        sel = {k: v for k, v in got.items()}
+        sel["status"] = got["status"][idx]; sel["obj"] = got["obj"][idx]; sel["iters"] = got["iters"][idx]
+        sel["x"] = np.concatenate([got["x"][sb.c_off[k]:sb.c_off[k] + 100] for k in idx])
+        sel["y"] = np.concatenate([got["y"][sb.b_off[k]:sb.b_off[k] + 100] for k in idx])
+        sel["basis"] = np.concatenate([got["basis"][sb.b_off[k]:sb.b_off[k] + 100] for k in idx])
+        compare(sub, sel, obj_rtol=rtol)
