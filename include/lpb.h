@@ -170,6 +170,27 @@ typedef struct {
 } lpb_stats;
 lpb_err lpb_get_stats(lpb_handle *handle, void *stream, lpb_stats *stats);
 
+/* lpb_solve for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this exists for plug-ins whose host framework owns all device
+ * memory through its own pool, and for loops where cudaMalloc / cudaFree are
+ * not allowed because they can synchronise the device.
+ *
+ * Same arguments and results as lpb_solve, minus the handle and workspace: it
+ * solves on the current CUDA device and takes its scratch from a 32 MiB
+ * device array inside the library (every GPU on which the library's module
+ * is loaded holds that array until the process exits).  It allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library call.
+ *   - The first call on each device resolves the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Returns LPB_ENOMEM, before launching anything, when the batch needs more
+ *     scratch than the array holds (lpb_workspace_size gives the need).
+ *   - Every call on a device shares the one array and starts by clearing its
+ *     counters and error word; calls that overlap on the GPU race on it, so
+ *     run them one after another. */
+lpb_err lpb_solve_noalloc(const lpb_batch *batch, const lpb_options *opt, const lpb_result *result,
+                          void *stream);
+
 /* Kernel timing.  lpb_profile_start(h, calls) makes the next `calls` (<= 256)
  * lpb_solve calls record a CUDA event pair on their stream around each of
  * their kernel passes (pass 0: every LP; pass 1: LPs needing more artificial

@@ -29,7 +29,7 @@ namespace {
 
 using namespace lpb;
 
-enum { CTR_Q1 = 0, CTR_Q2 = 1, CTR_Q3 = 2, CTR_DEFER = 4, CTR_RESOLVE = 5, CTR_N = 8 };
+enum { CTR_Q1 = 0, CTR_Q2 = 1, CTR_Q3 = 2, CTR_DEFER = 4, CTR_RESOLVE = 5, CTR_N = kCounters };
 
 class DeviceScope {
  public:
@@ -70,7 +70,7 @@ int auto_threads(int max_m, int max_n) {
   return t;
 }
 
-lpb_err make_pass(const lpb_handle *h, const lpb_batch *b, const lpb_options *o, bool fp64, int kcap,
+lpb_err make_pass(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o, bool fp64, int kcap,
                   int mode, Pass *p) {
   const int eb = fp64 ? 8 : 4;
   const bool refine = (mode == MODE_FP32_REFINE) && !fp64;
@@ -80,34 +80,34 @@ lpb_err make_pass(const lpb_handle *h, const lpb_batch *b, const lpb_options *o,
   p->threads = o->threads > 0 ? o->threads : auto_threads(b->max_m, b->max_n);
   if (p->threads < 32 || p->threads > 512 || (p->threads & 31)) return LPB_EINVAL;
   const size_t smem_s = tableau_smem_bytes(eb, false, b->max_m, b->max_n, kcap, p->threads, refine);
-  const bool want_gmem = o->kernel == LPB_KERNEL_GMEM || smem_s > h->smem_optin;
-  if (o->kernel == LPB_KERNEL_SMEM && smem_s > h->smem_optin) return LPB_EUNSUPPORTED;
+  const bool want_gmem = o->kernel == LPB_KERNEL_GMEM || smem_s > d.smem_optin;
+  if (o->kernel == LPB_KERNEL_SMEM && smem_s > d.smem_optin) return LPB_EUNSUPPORTED;
   int occ = 0;
   if (!want_gmem) {
     p->gmem = false;
     p->smem = smem_s;
     if (tableau_max_ctas_per_sm(eb, false, p->threads, p->smem, &occ) != cudaSuccess) return LPB_ECUDA;
     if (occ < 1) return LPB_EUNSUPPORTED;
-    p->grid = occ * h->sms;
+    p->grid = occ * d.sms;
   } else {
     p->gmem = true;
     p->smem = tableau_smem_bytes(eb, true, b->max_m, b->max_n, kcap, p->threads, refine);
-    if (p->smem > h->smem_optin) return LPB_EUNSUPPORTED;
+    if (p->smem > d.smem_optin) return LPB_EUNSUPPORTED;
     p->slot_bytes = tableau_slot_bytes(eb, b->max_m, b->max_n, kcap);
     if (tableau_max_ctas_per_sm(eb, true, p->threads, p->smem, &occ) != cudaSuccess) return LPB_ECUDA;
     if (occ < 1) return LPB_EUNSUPPORTED;
     // Keep the in-flight tableaux within about 3/4 of L2, but use every SM.
-    size_t fit = (h->l2_bytes * 3 / 4) / p->slot_bytes;
-    if (fit < size_t(h->sms)) fit = size_t(h->sms);
-    p->grid = int(fit < size_t(occ) * h->sms ? fit : size_t(occ) * h->sms);
+    size_t fit = (d.l2_bytes * 3 / 4) / p->slot_bytes;
+    if (fit < size_t(d.sms)) fit = size_t(d.sms);
+    p->grid = int(fit < size_t(occ) * d.sms ? fit : size_t(occ) * d.sms);
   }
   if (p->grid > b->count) p->grid = b->count > 0 ? b->count : 1;
   return LPB_OK;
 }
 
-lpb_err make_plan(const lpb_handle *h, const lpb_batch *b, const lpb_options *o, bool basis_given,
+lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o, bool basis_given,
                   Plan *pl) {
-  if (!h || !b || !o) return LPB_EINVAL;
+  if (!b || !o) return LPB_EINVAL;
   if (b->count < 0) return LPB_EINVAL;
   if (b->max_m < 1 || b->max_n < 1 || b->max_m > kMaxDim || b->max_n > kMaxDim) return LPB_EUNSUPPORTED;
   if (b->dtype != LPB_DTYPE_F32 && b->dtype != LPB_DTYPE_F64) return LPB_EINVAL;
@@ -119,14 +119,14 @@ lpb_err make_plan(const lpb_handle *h, const lpb_batch *b, const lpb_options *o,
   pl->feas_tol = o->feas_tol > 0 ? o->feas_tol : 1e-9;
   lpb_err e;
   const int mode = o->prec == LPB_FP64 ? MODE_FP64 : o->prec == LPB_FP32 ? MODE_FP32 : MODE_FP32_REFINE;
-  if ((e = make_pass(h, b, o, !fp32, 0, mode, &pl->pass[0])) != LPB_OK) return e;
-  if ((e = make_pass(h, b, o, !fp32, b->max_m, mode, &pl->pass[1])) != LPB_OK) return e;
+  if ((e = make_pass(d, b, o, !fp32, 0, mode, &pl->pass[0])) != LPB_OK) return e;
+  if ((e = make_pass(d, b, o, !fp32, b->max_m, mode, &pl->pass[1])) != LPB_OK) return e;
   pl->npass = 2;
   pl->resolve = o->prec == LPB_FP32_REFINE;
   if (pl->resolve) {
     lpb_options o64 = *o;
     if (o64.kernel == LPB_KERNEL_REG) o64.kernel = LPB_KERNEL_AUTO;
-    if ((e = make_pass(h, b, &o64, true, b->max_m, MODE_FP64, &pl->pass[2])) != LPB_OK) return e;
+    if ((e = make_pass(d, b, &o64, true, b->max_m, MODE_FP64, &pl->pass[2])) != LPB_OK) return e;
     pl->npass = 3;
   }
   pl->own_basis = pl->resolve && !basis_given;
@@ -146,16 +146,16 @@ lpb_err make_plan(const lpb_handle *h, const lpb_batch *b, const lpb_options *o,
   return LPB_OK;
 }
 
-TableauParams base_params(const lpb_handle *h, const lpb_batch *b, const lpb_result *r,
+TableauParams base_params(int32_t *ctr, uint32_t *err, const lpb_batch *b, const lpb_result *r,
                           const lpb_options *o, const Plan &pl, unsigned char *ws) {
   TableauParams p{};
   p.B = BatchDev{b->count, b->max_m, b->max_n, b->dtype, b->m, b->n, b->a_off, b->b_off, b->c_off,
                  b->A, b->b, b->c};
   p.R = ResultDev{r->status, r->iters, r->obj, r->x, r->y, r->basis};
   p.defer_items = reinterpret_cast<int32_t *>(ws + pl.off_defer);
-  p.defer_count = h->d_ctr + CTR_DEFER;
+  p.defer_count = ctr + CTR_DEFER;
   p.resolve_items = reinterpret_cast<int32_t *>(ws + pl.off_resolve);
-  p.resolve_count = h->d_ctr + CTR_RESOLVE;
+  p.resolve_count = ctr + CTR_RESOLVE;
   p.list_cap = b->count;
   p.bbuf = pl.own_basis ? reinterpret_cast<int32_t *>(ws + pl.off_basis) : r->basis;
   p.bpacked = pl.own_basis ? 0 : 1;
@@ -164,11 +164,63 @@ TableauParams base_params(const lpb_handle *h, const lpb_batch *b, const lpb_res
   p.eps_p = pl.eps_p;
   p.eps_d = pl.eps_d;
   p.feas_tol = pl.feas_tol;
-  p.err = h->d_err;
+  p.err = err;
   return p;
 }
 
+DeviceInfo device_info(const lpb_handle *h) { return DeviceInfo{h->sms, h->smem_optin, h->l2_bytes}; }
+
 }  // namespace
+
+namespace lpb {
+
+lpb_err solve_workspace_bytes(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
+                              bool basis_given, size_t *bytes) {
+  Plan pl;
+  const lpb_err e = make_plan(d, b, o, basis_given, &pl);
+  if (e != LPB_OK) return e;
+  *bytes = pl.total;
+  return LPB_OK;
+}
+
+lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_batch *b,
+                  const lpb_options *o, const lpb_result *r, void *ws, size_t ws_bytes, cudaStream_t s,
+                  cudaEvent_t *prof_ev, bool *prof_ran) {
+  Plan pl;
+  lpb_err e = make_plan(d, b, o, r->basis != nullptr, &pl);
+  if (e != LPB_OK) return e;
+  if (ws_bytes < pl.total || (pl.total > 0 && !ws)) return LPB_ENOMEM;
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return LPB_EINVAL;
+  unsigned char *w = static_cast<unsigned char *>(ws);
+  if (cudaMemsetAsync(ctr, 0, kCounters * sizeof(int32_t), s) != cudaSuccess) return LPB_ECUDA;
+  for (int i = 0; i < pl.npass; ++i) {
+    const Pass &ps = pl.pass[i];
+    cudaEvent_t *ev = prof_ev ? prof_ev + i * 2 : nullptr;
+    if (ev && cudaEventRecord(ev[0], s) != cudaSuccess) return LPB_ECUDA;
+    TableauParams p = base_params(ctr, err, b, r, o, pl, w);
+    p.kcap = ps.kcap;
+    p.mode = ps.mode;
+    p.slot_bytes = ps.slot_bytes;
+    p.queue = ctr + (i == 0 ? CTR_Q1 : i == 1 ? CTR_Q2 : CTR_Q3);
+    if (i == 0) {
+      p.in = WorkList{nullptr, nullptr};
+    } else if (i == 1) {
+      p.in = WorkList{p.defer_items, p.defer_count};
+      p.defer_items = nullptr;   // kcap = max_m: nothing is deferred again
+    } else {
+      p.in = WorkList{p.resolve_items, p.resolve_count};
+      p.warm = 1;
+    }
+    if (launch_tableau(p, ps.fp64, ps.gmem, ps.grid, ps.threads, ps.smem, s) != cudaSuccess) return LPB_ECUDA;
+    if (ev) {
+      if (cudaEventRecord(ev[1], s) != cudaSuccess) return LPB_ECUDA;
+      prof_ran[i] = true;
+    }
+  }
+  return LPB_OK;
+}
+
+}  // namespace lpb
 
 extern "C" {
 
@@ -234,12 +286,8 @@ lpb_err lpb_workspace_size(lpb_handle *h, const lpb_batch *b, const lpb_options 
   if (!h || !b || !o || !bytes) return LPB_EINVAL;
   DeviceScope ds(h->device);
   if (!ds.ok()) return LPB_ECUDA;
-  Plan pl;
   // Size for the worst case: the basis may have to live in the workspace.
-  const lpb_err e = make_plan(h, b, o, false, &pl);
-  if (e != LPB_OK) return e;
-  *bytes = pl.total;
-  return LPB_OK;
+  return solve_workspace_bytes(device_info(h), b, o, false, bytes);
 }
 
 lpb_err lpb_solve(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const lpb_result *r,
@@ -251,41 +299,13 @@ lpb_err lpb_solve(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const
   if (!r->status || !r->obj || !r->x) return LPB_EINVAL;
   DeviceScope ds(h->device);
   if (!ds.ok()) return LPB_ECUDA;
-  Plan pl;
-  lpb_err e = make_plan(h, b, o, r->basis != nullptr, &pl);
-  if (e != LPB_OK) return e;
-  if (ws_bytes < pl.total || (pl.total > 0 && !ws)) return LPB_ENOMEM;
-  if (reinterpret_cast<uintptr_t>(ws) & 255) return LPB_EINVAL;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  unsigned char *w = static_cast<unsigned char *>(ws);
-  if (cudaMemsetAsync(h->d_ctr, 0, CTR_N * sizeof(int32_t), s) != cudaSuccess) return LPB_ECUDA;
   const bool prof = h->prof_ev && h->prof_n < h->prof_cap;
-  for (int i = 0; i < pl.npass; ++i) {
-    const Pass &ps = pl.pass[i];
-    cudaEvent_t *ev = prof ? h->prof_ev + (size_t(h->prof_n) * 3 + i) * 2 : nullptr;
-    if (ev && cudaEventRecord(ev[0], s) != cudaSuccess) return LPB_ECUDA;
-    TableauParams p = base_params(h, b, r, o, pl, w);
-    p.kcap = ps.kcap;
-    p.mode = ps.mode;
-    p.slot_bytes = ps.slot_bytes;
-    p.queue = h->d_ctr + (i == 0 ? CTR_Q1 : i == 1 ? CTR_Q2 : CTR_Q3);
-    if (i == 0) {
-      p.in = WorkList{nullptr, nullptr};
-    } else if (i == 1) {
-      p.in = WorkList{p.defer_items, p.defer_count};
-      p.defer_items = nullptr;   // kcap = max_m: nothing is deferred again
-    } else {
-      p.in = WorkList{p.resolve_items, p.resolve_count};
-      p.warm = 1;
-    }
-    if (launch_tableau(p, ps.fp64, ps.gmem, ps.grid, ps.threads, ps.smem, s) != cudaSuccess) return LPB_ECUDA;
-    if (ev) {
-      if (cudaEventRecord(ev[1], s) != cudaSuccess) return LPB_ECUDA;
-      h->prof_ran[h->prof_n * 3 + i] = true;
-    }
-  }
-  if (prof) ++h->prof_n;
-  return LPB_OK;
+  const lpb_err e = run_solve(device_info(h), h->d_ctr, h->d_err, b, o, r, ws, ws_bytes,
+                              static_cast<cudaStream_t>(stream),
+                              prof ? h->prof_ev + size_t(h->prof_n) * 3 * 2 : nullptr,
+                              prof ? h->prof_ran + h->prof_n * 3 : nullptr);
+  if (e == LPB_OK && prof) ++h->prof_n;
+  return e;
 }
 
 lpb_err lpb_profile_start(lpb_handle *h, int32_t calls) {

@@ -139,4 +139,22 @@ cudaError_t launch_tableau(const TableauParams &p, bool fp64, bool gmem, int gri
 size_t hyperbox_smem_bytes(int n, int elem_bytes, bool shared_box);
 cudaError_t launch_hyperbox(const HyperboxParams &p, cudaStream_t s);
 
+// ---- a whole solve (lpb_api.cu) -------------------------------------------
+
+struct DeviceInfo {
+  int sms;
+  size_t smem_optin, l2_bytes;
+};
+
+constexpr int kCounters = 8;   // device int32 work queues and list lengths of one solve
+
+// Workspace bytes of a solve (`basis_given`: the caller passes a basis array).
+lpb_err solve_workspace_bytes(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
+                              bool basis_given, size_t *bytes);
+// Zero `ctr` (kCounters device ints) and launch every pass of a solve on `s`,
+// with scratch from `ws`.  prof_ev (3 pairs) / prof_ran (3 flags) may be null.
+lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_batch *b,
+                  const lpb_options *o, const lpb_result *r, void *ws, size_t ws_bytes, cudaStream_t s,
+                  cudaEvent_t *prof_ev, bool *prof_ran);
+
 }  // namespace lpb
