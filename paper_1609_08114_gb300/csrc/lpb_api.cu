@@ -50,6 +50,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Pass {
   bool fp64 = false, gmem = false;
   int kcap = 0, mode = MODE_FP64, grid = 0, threads = 128;
+  int reg = -1;              // >= 0: register-resident kernel configuration
   size_t smem = 0, slot_bytes = 0;
 };
 
@@ -119,7 +120,31 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   pl->feas_tol = o->feas_tol > 0 ? o->feas_tol : 1e-9;
   lpb_err e;
   const int mode = o->prec == LPB_FP64 ? MODE_FP64 : o->prec == LPB_FP32 ? MODE_FP32 : MODE_FP32_REFINE;
-  if ((e = make_pass(d, b, o, !fp32, 0, mode, &pl->pass[0])) != LPB_OK) return e;
+  int reg = (fp32 && (o->kernel == LPB_KERNEL_AUTO || o->kernel == LPB_KERNEL_REG))
+                      ? reg_pick(b->max_m, b->max_n, o->threads > 0 ? o->threads / 32 : 0) : -1;
+  int reg_occ = 0, reg_threads = 0;
+  size_t reg_smem = 0;
+  if (reg >= 0) {
+    if (reg_occupancy(reg, b->max_m, b->max_n, b->dtype, &reg_occ, &reg_threads, &reg_smem) != cudaSuccess)
+      return LPB_ECUDA;
+    if (reg_smem > d.smem_optin || reg_occ < 1) reg = -1;   // the input does not fit on chip
+  }
+  if (o->kernel == LPB_KERNEL_REG && reg < 0) return LPB_EUNSUPPORTED;
+  if (reg >= 0) {   // pass 0: register-resident FP32 tableau
+    Pass &p0 = pl->pass[0];
+    p0.fp64 = false;
+    p0.mode = mode;
+    p0.reg = reg;
+    p0.threads = reg_threads;
+    p0.smem = reg_smem;
+    p0.grid = reg_occ * d.sms;
+    if (p0.grid > b->count) p0.grid = b->count > 0 ? b->count : 1;
+  } else if ((e = make_pass(d, b, o, !fp32, 0, mode, &pl->pass[0])) != LPB_OK) {
+    return e;
+  }
+  lpb_options o1 = *o;   // later passes run the shared-memory / L2-slot kernel
+  if (o1.kernel == LPB_KERNEL_REG) { o1.kernel = LPB_KERNEL_AUTO; o1.threads = 0; }
+  o = &o1;
   if ((e = make_pass(d, b, o, !fp32, b->max_m, mode, &pl->pass[1])) != LPB_OK) return e;
   pl->npass = 2;
   pl->resolve = o->prec == LPB_FP32_REFINE;
@@ -211,7 +236,9 @@ lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_ba
       p.in = WorkList{p.resolve_items, p.resolve_count};
       p.warm = 1;
     }
-    if (launch_tableau(p, ps.fp64, ps.gmem, ps.grid, ps.threads, ps.smem, s) != cudaSuccess) return LPB_ECUDA;
+    const cudaError_t ce = ps.reg >= 0 ? launch_reg(p, ps.reg, ps.grid, ps.smem, s)
+                                       : launch_tableau(p, ps.fp64, ps.gmem, ps.grid, ps.threads, ps.smem, s);
+    if (ce != cudaSuccess) return LPB_ECUDA;
     if (ev) {
       if (cudaEventRecord(ev[1], s) != cudaSuccess) return LPB_ECUDA;
       prof_ran[i] = true;

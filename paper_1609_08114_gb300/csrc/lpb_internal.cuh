@@ -54,6 +54,45 @@ __device__ __forceinline__ double ld_in(const void *p, int64_t i, int dt) {
                              : static_cast<double>(__ldg(static_cast<const float *>(p) + i));
 }
 
+// Round a double to the nearest float (ties to even) with integer operations:
+// on this GPU the FP64 unit, which also performs double->float conversions,
+// runs at a small fraction of the FP32 rate.  Normal results take the integer
+// path (the top 23 of the 52 mantissa bits, rounded on the 29 dropped bits);
+// zero keeps its sign; subnormal, overflowing and non-finite values, which the
+// solver does not expect, use the hardware conversion.
+__device__ __forceinline__ float d2f_rn(double d) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(d));
+  const unsigned hi = unsigned(u >> 32), lo = unsigned(u);
+  const unsigned sign = hi & 0x80000000u, ahi = hi & 0x7fffffffu;
+  const unsigned e = ahi >> 20;
+  if (e >= 897u && e <= 1150u) {          // biased exponents of the normal floats
+    unsigned f = ((ahi - (896u << 20)) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    f += (rem > 0x10000000u) || (rem == 0x10000000u && (f & 1u));
+    return __uint_as_float(sign | f);
+  }
+  if ((ahi | lo) == 0u) return __uint_as_float(sign);
+  return __double2float_rn(d);
+}
+
+// Finite test on the exponent bits (no FP64 instruction).
+__device__ __forceinline__ bool finite_bits(double d) {
+  return (unsigned(static_cast<unsigned long long>(__double_as_longlong(d)) >> 32) & 0x7ff00000u) != 0x7ff00000u;
+}
+
+// Input element `i` as the tableau's type T.
+template <typename T>
+__device__ __forceinline__ T ld_as(const void *p, int64_t i, int dt);
+template <>
+__device__ __forceinline__ float ld_as<float>(const void *p, int64_t i, int dt) {
+  return dt == LPB_DTYPE_F64 ? d2f_rn(__ldg(static_cast<const double *>(p) + i))
+                             : __ldg(static_cast<const float *>(p) + i);
+}
+template <>
+__device__ __forceinline__ double ld_as<double>(const void *p, int64_t i, int dt) {
+  return ld_in(p, i, dt);
+}
+
 // (value, key) order: smaller value first, then smaller key.
 template <typename T>
 __device__ __forceinline__ void keep_better(T &v, int &k, T ov, int ok) {
@@ -69,6 +108,29 @@ __device__ __forceinline__ void warp_argmin(T &v, int &k) {
     keep_better(v, k, ov, ok);
   }
 }
+
+// Order-preserving image of a float in the unsigned integers (negative values
+// have their bits inverted, non-negative ones get the sign bit set), so that
+// the warp reduction instruction can take the minimum.
+__device__ __forceinline__ unsigned f2ord(float f) {
+  const unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned o) {
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// (value, key) arg-min of a warp with two warp-reduction instructions: the
+// least value, then the least key among the lanes holding it.  Keys are >= 0.
+__device__ __forceinline__ void warp_argmin_f32(float &v, int &k) {
+  const unsigned o = f2ord(v);
+  const unsigned mo = __reduce_min_sync(kFull, o);
+  const unsigned kk = (o == mo) ? unsigned(k) : 0xffffffffu;
+  k = int(__reduce_min_sync(kFull, kk));
+  v = ord2f(mo);
+}
+template <>
+__device__ __forceinline__ void warp_argmin<float>(float &v, int &k) { warp_argmin_f32(v, k); }
 
 // Every thread of the block receives the block-wide minimum.  `bv`/`bk` hold
 // one slot per warp; a call site must not reuse them before the block has
@@ -136,6 +198,12 @@ size_t tableau_slot_bytes(int elem_bytes, int max_m, int max_n, int kcap);
 cudaError_t tableau_max_ctas_per_sm(int elem_bytes, bool gmem, int threads, size_t smem, int *ctas);
 cudaError_t launch_tableau(const TableauParams &p, bool fp64, bool gmem, int grid, int threads,
                            size_t smem, cudaStream_t s);
+// Register-resident FP32 kernel (simplex_reg.cu): configuration index for
+// (max_m, max_n) or -1, its occupancy, and its launch.  It defers to the
+// defer list every LP it does not take (Phase I, sizes, non-finite data).
+int reg_pick(int max_m, int max_n, int want_warps);
+cudaError_t reg_occupancy(int cfg, int max_m, int max_n, int dtype, int *ctas, int *threads, size_t *smem);
+cudaError_t launch_reg(const TableauParams &p, int cfg, int grid, size_t smem, cudaStream_t s);
 size_t hyperbox_smem_bytes(int n, int elem_bytes, bool shared_box);
 cudaError_t launch_hyperbox(const HyperboxParams &p, cudaStream_t s);
 

@@ -237,26 +237,45 @@ __device__ bool build_tableau(Tab<T> &S, const BatchDev &B, int lp, int64_t aoff
   }
   __syncthreads();
   bool bad = false;
-  for (int i = wid; i < m; i += nw) {
-    const bool neg = S.basic[i] >= n + m;
-    const T s = neg ? T(-1) : T(1);
-    T *row = S.t + size_t(i) * ld;
-    const int64_t ar = aoff + int64_t(i) * n;
-    for (int j = lane; j < n; j += 32) {
-      const double a = ld_in(B.A, ar + j, B.dtype);
-      bad |= !isfinite(a);
-      row[j] = s * T(a);
-    }
-    if (lane == 0) {
-      const double bi = ld_in(B.b, boff + i, B.dtype);
-      bad |= !isfinite(bi);
-      row[nc] = s * T(bi);
+  // Rows go to warps, columns to lanes; each lane keeps kU x kU loads in flight
+  // before it stores, so a row block costs one memory round trip.
+  constexpr int kU = 4;
+  for (int i0 = wid; i0 < m; i0 += nw * kU) {
+    for (int j0 = lane; j0 < n; j0 += 32 * kU) {
+      T v[kU][kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u)
+#pragma unroll
+        for (int w = 0; w < kU; ++w) {
+          const int i = i0 + u * nw, j = j0 + 32 * w;
+          v[u][w] = (i < m && j < n) ? ld_as<T>(B.A, aoff + int64_t(i) * n + j, B.dtype) : T(0);
+        }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int i = i0 + u * nw;
+        if (i >= m) continue;
+        const T s = S.basic[i] >= n + m ? T(-1) : T(1);
+        T *row = S.t + size_t(i) * ld;
+#pragma unroll
+        for (int w = 0; w < kU; ++w) {
+          const int j = j0 + 32 * w;
+          if (j < n) {
+            bad |= !isfinite(v[u][w]);
+            row[j] = s * v[u][w];
+          }
+        }
+      }
     }
   }
+  for (int i = tid; i < m; i += nt) {
+    const T bi = ld_as<T>(B.b, boff + i, B.dtype);
+    bad |= !isfinite(bi);
+    S.t[size_t(i) * ld + nc] = S.basic[i] >= n + m ? -bi : bi;
+  }
   for (int j = tid; j < n; j += nt) {
-    const double cj = ld_in(B.c, coff + j, B.dtype);
+    const T cj = ld_as<T>(B.c, coff + j, B.dtype);
     bad |= !isfinite(cj);
-    S.t[size_t(m) * ld + j] = -T(cj);
+    S.t[size_t(m) * ld + j] = -cj;
   }
   bad = __syncthreads_or(bad);
   if (S.k) {   // Phase-I row: w = -(sum of artificials) in the non-basic variables
@@ -385,6 +404,7 @@ __device__ bool refine_and_verify(Tab<float> &S, const BatchDev &B, const Result
   for (int i = tid; i < m; i += nt) {
     double r = ld_in(B.b, boff + i, dt);
     const int64_t ar = aoff + int64_t(i) * n;
+#pragma unroll 4
     for (int q = 0; q < nsb; ++q) {
       const int t = sb[q];
       r = fma(-ld_in(B.A, ar + S.basic[t], dt), xb[t], r);
@@ -396,6 +416,7 @@ __device__ bool refine_and_verify(Tab<float> &S, const BatchDev &B, const Result
   for (int q = tid; q < nsb; q += nt) {
     const int t = sb[q], j = S.basic[t];
     double r = ld_in(B.c, coff + j, dt);
+#pragma unroll 4
     for (int p = 0; p < nns; ++p) {
       const int kk = S.nonb[ns[p]] - n;
       r = fma(-ld_in(B.A, aoff + int64_t(kk) * n + j, dt), yv[kk], r);
@@ -427,24 +448,34 @@ __device__ bool refine_and_verify(Tab<float> &S, const BatchDev &B, const Result
     yv[S.nonb[col] - n] += double(d);
   }
   __syncthreads();
-  // Objective, b^T y and the feasibility checks.
+  // FP64 KKT certificate of the pair that is written out (x: the structural
+  // part of x_B; y: the slack duals): x >= 0, A x <= b, y >= 0, A^T y >= c and
+  // c^T x = b^T y, each to tol scaled by the data.
   double cx = 0.0, by = 0.0;
   int bad = 0;
   const double tp = tol * (1.0 + bmax), td = tol * (1.0 + cmax);
-  for (int q = tid; q < nsb; q += nt) cx = fma(ld_in(B.c, coff + S.basic[sb[q]], dt), xb[sb[q]], cx);
+  for (int q = tid; q < nsb; q += nt) {
+    bad |= !(xb[sb[q]] >= -tp);
+    cx = fma(ld_in(B.c, coff + S.basic[sb[q]], dt), xb[sb[q]], cx);
+  }
   for (int p = tid; p < nns; p += nt) {
     const int kk = S.nonb[ns[p]] - n;
     by = fma(ld_in(B.b, boff + kk, dt), yv[kk], by);
     bad |= !(yv[kk] >= -td);
   }
-  for (int i = tid; i < m; i += nt) bad |= !(xb[i] >= -tp);
-  for (int j = tid; j < nc; j += nt) {   // reduced costs A_j^T y - c_j of non-basic structurals
-    const int v = S.nonb[j];
-    if (v >= n) continue;
-    double d = -ld_in(B.c, coff + v, dt);
+  for (int i = tid; i < m; i += nt) {     // slack b_i - A_i x of every row
+    double s = ld_in(B.b, boff + i, dt);
+    const int64_t ar = aoff + int64_t(i) * n;
+#pragma unroll 4
+    for (int q = 0; q < nsb; ++q) s = fma(-ld_in(B.A, ar + S.basic[sb[q]], dt), xb[sb[q]], s);
+    bad |= !(s >= -tp);
+  }
+  for (int j = tid; j < n; j += nt) {     // reduced cost A_j^T y - c_j of every column
+    double d = -ld_in(B.c, coff + j, dt);
+#pragma unroll 4
     for (int p = 0; p < nns; ++p) {
       const int kk = S.nonb[ns[p]] - n;
-      d = fma(ld_in(B.A, aoff + int64_t(kk) * n + v, dt), yv[kk], d);
+      d = fma(ld_in(B.A, aoff + int64_t(kk) * n + j, dt), yv[kk], d);
     }
     bad |= !(d >= -td);
   }

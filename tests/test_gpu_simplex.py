@@ -40,13 +40,27 @@ def test_type1_m16_full_batch(solver, prec, rtol):
     assert np.all(got["status"] == 0) and n_unique > 900
 
 
-@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-9), ("fp32_refine", 1e-8)])
-@pytest.mark.parametrize("kernel", [1, 2])   # shared-memory and L2-slot tableau classes
-def test_type1_m100_sample(solver, prec, rtol, kernel):
-    """300 LPs of the m = n = 100 workload, through both tableau classes."""
+@pytest.mark.parametrize("prec,rtol,kernel,threads", [
+    ("fp64", 1e-9, 1, 0), ("fp64", 1e-9, 2, 0),                 # shared-memory, L2-slot tableau
+    ("fp32_refine", 1e-8, 1, 0), ("fp32_refine", 1e-8, 2, 0),
+    ("fp32_refine", 1e-8, 3, 128), ("fp32_refine", 1e-8, 3, 256),  # register tableau, 4 or 8 warps
+    ("fp32", 1e-5, 3, 0)])
+def test_type1_m100_sample(solver, prec, rtol, kernel, threads):
+    """300 LPs of the m = n = 100 workload through every kernel class."""
     sb = synth.type1(50000, 100, 100, seed=1, first=1000, stop=1300)
-    got = run(solver, sb, prec, kernel=kernel)
-    compare(sb, got, obj_rtol=rtol)
+    got = run(solver, sb, prec, kernel=kernel, threads=threads)
+    compare(sb, got, obj_rtol=rtol, kkt_tol=1e-8 if prec != "fp32" else 1e-4,
+            check_unique=prec != "fp32")
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (5, 5), (16, 16), (31, 20), (20, 31), (40, 63), (63, 63),
+                                 (100, 100), (127, 103), (120, 127)])
+def test_register_kernel_shapes(solver, m, n):
+    """Every register-tableau configuration at and near its size limits (ragged tiles)."""
+    sb = synth.type1(120, m, n, seed=m * 1000 + n)
+    got = run(solver, sb, "fp32_refine", kernel=3)
+    compare(sb, got, obj_rtol=1e-8)
+    assert solver.stats()["deferred"] == 0
 
 
 @pytest.mark.parametrize("prec,rtol", [("fp64", 1e-9), ("fp32_refine", 1e-8)])
