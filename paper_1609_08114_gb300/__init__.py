@@ -166,6 +166,26 @@ class Solver:
                                       _ptr(ws), ws.numel(), _stream_handle(self.device)), "lpb_solve")
         return res
 
+    def solve_backward(self, batch: LPBatch, res: SolveResult, g_obj: torch.Tensor | None,
+                       g_x: torch.Tensor | None):
+        """Vector-Jacobian product through the optimal basis of ``res`` (see lpb_solve_backward).
+        Returns FP64 ``(g_c, g_b, g_A)`` packed like ``c``, ``b`` and ``A``."""
+        dev = batch.device
+        g_c = torch.empty(batch.c.numel(), dtype=torch.float64, device=dev)
+        g_b = torch.empty(batch.b.numel(), dtype=torch.float64, device=dev)
+        g_A = torch.empty(batch.A.numel(), dtype=torch.float64, device=dev)
+        if g_obj is not None:
+            g_obj = g_obj.to(torch.float64).contiguous()
+        if g_x is not None:
+            g_x = g_x.to(torch.float64).contiguous()
+        opt = self.options()
+        ws = self.workspace(self.workspace_size(batch, opt))
+        cb, cr = batch.cstruct(), res.cstruct()
+        _lib.check(self.lib.lpb_solve_backward(self.h, ctypes.byref(cb), ctypes.byref(opt), ctypes.byref(cr),
+                                               _ptr(g_obj), _ptr(g_x), _ptr(g_c), _ptr(g_b), _ptr(g_A), _ptr(ws),
+                                               ws.numel(), _stream_handle(self.device)), "lpb_solve_backward")
+        return g_c, g_b, g_A
+
     def hyperbox(self, c: torch.Tensor, l: torch.Tensor, u: torch.Tensor, want_x: bool = False,
                  obj: torch.Tensor | None = None, x: torch.Tensor | None = None):
         """Support functions over boxes (Section 6, Eq. 8): ``c[count, n]`` with ``l, u`` of
@@ -205,3 +225,8 @@ class Solver:
         if code not in (_lib.OK, _lib.EDEVICE):
             _lib.check(code, "lpb_sync_error")
         return int(w.value)
+
+
+from .autograd import solve  # noqa: E402  (differentiable solve; needs Solver and LPBatch above)
+
+__all__.append("solve")

@@ -29,7 +29,7 @@ namespace {
 
 using namespace lpb;
 
-enum { CTR_Q1 = 0, CTR_Q2 = 1, CTR_Q3 = 2, CTR_DEFER = 4, CTR_RESOLVE = 5, CTR_N = kCounters };
+enum { CTR_Q1 = 0, CTR_Q2 = 1, CTR_Q3 = 2, CTR_DEFER = 4, CTR_RESOLVE = 5, CTR_BWD = 6, CTR_N = kCounters };
 
 class DeviceScope {
  public:
@@ -314,7 +314,16 @@ lpb_err lpb_workspace_size(lpb_handle *h, const lpb_batch *b, const lpb_options 
   DeviceScope ds(h->device);
   if (!ds.ok()) return LPB_ECUDA;
   // Size for the worst case: the basis may have to live in the workspace.
-  return solve_workspace_bytes(device_info(h), b, o, false, bytes);
+  const lpb_err e = solve_workspace_bytes(device_info(h), b, o, false, bytes);
+  if (e != LPB_OK) return e;
+  // lpb_solve_backward needs FP64 elimination slots only for large systems.
+  const size_t smem = backward_smem_bytes(b->max_m, b->max_n);
+  int grid = 0;
+  if (smem <= h->smem_optin && backward_grid(h->sms, smem, &grid) == cudaSuccess) {
+    const size_t need = backward_slot_bytes(b->max_m, b->max_n) * size_t(grid);
+    if (need > *bytes) *bytes = need;
+  }
+  return LPB_OK;
 }
 
 lpb_err lpb_solve(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const lpb_result *r,
@@ -373,9 +382,41 @@ lpb_err lpb_profile_read(lpb_handle *h, float *ms, int32_t max_calls, int32_t *n
 lpb_err lpb_solve_backward(lpb_handle *h, const lpb_batch *b, const lpb_options *o,
                            const lpb_result *r, const double *g_obj, const double *g_x, double *g_c,
                            double *g_b, double *g_A, void *ws, size_t ws_bytes, void *stream) {
-  (void)h; (void)b; (void)o; (void)r; (void)g_obj; (void)g_x; (void)g_c; (void)g_b; (void)g_A;
-  (void)ws; (void)ws_bytes; (void)stream;
-  return LPB_EUNSUPPORTED;
+  if (!h || !b || !o || !r) return LPB_EINVAL;
+  if (b->count < 0) return LPB_EINVAL;
+  if (b->count == 0) return LPB_OK;
+  if (!b->m || !b->n || !b->a_off || !b->b_off || !b->c_off || !b->A) return LPB_EINVAL;
+  if (!r->status || !r->x || !r->y || !r->basis || !g_c || !g_b || !g_A) return LPB_EINVAL;
+  if (b->max_m < 1 || b->max_n < 1 || b->max_m > kMaxDim || b->max_n > kMaxDim) return LPB_EUNSUPPORTED;
+  if (b->dtype != LPB_DTYPE_F32 && b->dtype != LPB_DTYPE_F64) return LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  const size_t smem = backward_smem_bytes(b->max_m, b->max_n);
+  if (smem > h->smem_optin) return LPB_EUNSUPPORTED;
+  int grid = 0;
+  if (backward_grid(h->sms, smem, &grid) != cudaSuccess) return LPB_ECUDA;
+  if (grid > b->count) grid = b->count;
+  const size_t slot = backward_slot_bytes(b->max_m, b->max_n);
+  if (slot * size_t(grid) > ws_bytes || (slot && !ws)) return LPB_ENOMEM;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  BackwardParams p{};
+  p.B = BatchDev{b->count, b->max_m, b->max_n, b->dtype, b->m, b->n, b->a_off, b->b_off, b->c_off,
+                 b->A, b->b, b->c};
+  p.status = r->status;
+  p.basis = r->basis;
+  p.x = r->x;
+  p.y = r->y;
+  p.g_obj = g_obj;
+  p.g_x = g_x;
+  p.g_c = g_c;
+  p.g_b = g_b;
+  p.g_A = g_A;
+  p.slots = ws;
+  p.slot_bytes = slot;
+  p.queue = h->d_ctr + CTR_BWD;
+  p.err = h->d_err;
+  if (cudaMemsetAsync(p.queue, 0, sizeof(int32_t), s) != cudaSuccess) return LPB_ECUDA;
+  return launch_backward(p, grid, smem, s) == cudaSuccess ? LPB_OK : LPB_ECUDA;
 }
 
 lpb_err lpb_hyperbox(lpb_handle *h, int64_t count, int32_t n, int32_t dtype, const void *c,

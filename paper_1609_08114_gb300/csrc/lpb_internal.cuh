@@ -184,6 +184,18 @@ struct TableauParams {
   uint32_t *err;
 };
 
+struct BackwardParams {
+  BatchDev B;
+  const int32_t *status, *basis;   // forward result: basis packed like b (required)
+  const double *x, *y;
+  const double *g_obj, *g_x;       // upstream gradients (either may be null)
+  double *g_c, *g_b, *g_A;
+  void *slots;                     // per-CTA FP64 elimination slots for large systems
+  size_t slot_bytes;
+  int32_t *queue;
+  uint32_t *err;
+};
+
 struct HyperboxParams {
   int64_t count;
   int n, dtype, shared_box;
@@ -206,6 +218,11 @@ cudaError_t reg_occupancy(int cfg, int max_m, int max_n, int dtype, int *ctas, i
 cudaError_t launch_reg(const TableauParams &p, int cfg, int grid, size_t smem, cudaStream_t s);
 size_t hyperbox_smem_bytes(int n, int elem_bytes, bool shared_box);
 cudaError_t launch_hyperbox(const HyperboxParams &p, cudaStream_t s);
+// Backward kernel (backward.cu).
+size_t backward_smem_bytes(int max_m, int max_n);
+size_t backward_slot_bytes(int max_m, int max_n);
+cudaError_t backward_grid(int sms, size_t smem, int *grid);
+cudaError_t launch_backward(const BackwardParams &p, int grid, size_t smem, cudaStream_t s);
 
 // ---- a whole solve (lpb_api.cu) -------------------------------------------
 
