@@ -29,7 +29,8 @@ namespace {
 
 using namespace lpb;
 
-enum { CTR_Q1 = 0, CTR_Q2 = 1, CTR_Q3 = 2, CTR_DEFER = 4, CTR_RESOLVE = 5, CTR_BWD = 6, CTR_N = kCounters };
+// Handle counters (the per-pass work queues live in the workspace).
+enum { CTR_DEFER = 4, CTR_RESOLVE = 5, CTR_BWD = 6, CTR_N = kCounters };
 
 class DeviceScope {
  public:
@@ -47,19 +48,30 @@ class DeviceScope {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+enum ListKind { LIST_ALL = 0, LIST_CLASS = 1, LIST_DEFER = 2, LIST_RESOLVE = 3 };
+
 struct Pass {
   bool fp64 = false, gmem = false;
   int kcap = 0, mode = MODE_FP64, grid = 0, threads = 128;
   int reg = -1;              // >= 0: register-resident kernel configuration
+  int list = LIST_ALL, cls = 0;
+  int lim_m = 0, lim_n = 0;  // size bounds of the launch
+  int group = 0;             // timing group: 0 first solve, 1 Phase-I pass, 2 FP64 re-solve
   size_t smem = 0, slot_bytes = 0;
 };
 
+constexpr int kMaxPasses = kMaxClasses + 2;
+
 struct Plan {
-  Pass pass[3];
+  Pass pass[kMaxPasses];
   int npass = 0;
-  bool resolve = false;      // pass 2 (index 2) re-solves FP32 failures in FP64
+  bool classes = false;      // a classify step splits the batch into size classes
+  int nclass = 0;
+  int cls_m[kMaxClasses] = {}, cls_n[kMaxClasses] = {};
+  bool resolve = false;      // the last pass re-solves FP32 failures in FP64
   bool own_basis = false;    // basis lives in the workspace
-  size_t off_defer = 0, off_resolve = 0, off_basis = 0, off_slots = 0, total = 0;
+  size_t off_defer = 0, off_resolve = 0, off_basis = 0, off_lists = 0, off_hist = 0, off_cctr = 0,
+         off_slots = 0, total = 0;
   double eps_p = 0, eps_d = 0, feas_tol = 0;
 };
 
@@ -106,6 +118,20 @@ lpb_err make_pass(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   return LPB_OK;
 }
 
+lpb_err reg_pass(const DeviceInfo &d, const lpb_batch *b, int cfg, int lim_m, int lim_n, int mode, Pass *p) {
+  int occ = 0;
+  if (reg_occupancy(cfg, lim_m, lim_n, b->dtype, &occ, &p->threads, &p->smem) != cudaSuccess) return LPB_ECUDA;
+  if (p->smem > d.smem_optin || occ < 1) return LPB_EUNSUPPORTED;   // the input does not fit on chip
+  p->fp64 = false;
+  p->mode = mode;
+  p->reg = cfg;
+  p->lim_m = lim_m;
+  p->lim_n = lim_n;
+  p->grid = occ * d.sms;
+  if (p->grid > b->count) p->grid = b->count > 0 ? b->count : 1;
+  return LPB_OK;
+}
+
 lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o, bool basis_given,
                   Plan *pl) {
   if (!b || !o) return LPB_EINVAL;
@@ -120,52 +146,109 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   pl->feas_tol = o->feas_tol > 0 ? o->feas_tol : 1e-9;
   lpb_err e;
   const int mode = o->prec == LPB_FP64 ? MODE_FP64 : o->prec == LPB_FP32 ? MODE_FP32 : MODE_FP32_REFINE;
-  int reg = (fp32 && (o->kernel == LPB_KERNEL_AUTO || o->kernel == LPB_KERNEL_REG))
-                      ? reg_pick(b->max_m, b->max_n, o->threads > 0 ? o->threads / 32 : 0) : -1;
-  int reg_occ = 0, reg_threads = 0;
-  size_t reg_smem = 0;
-  if (reg >= 0) {
-    if (reg_occupancy(reg, b->max_m, b->max_n, b->dtype, &reg_occ, &reg_threads, &reg_smem) != cudaSuccess)
-      return LPB_ECUDA;
-    if (reg_smem > d.smem_optin || reg_occ < 1) reg = -1;   // the input does not fit on chip
+  const int want_w = o->threads > 0 ? o->threads / 32 : 8;
+  lpb_options og = *o;          // options of the shared-memory / L2-slot kernel passes
+  if (og.kernel == LPB_KERNEL_REG) { og.kernel = LPB_KERNEL_AUTO; og.threads = 0; }
+  int np = 0;
+  if (fp32 && o->kernel == LPB_KERNEL_AUTO) {
+    // Size classes: the register-tableau templates with `want_w` warps in
+    // increasing size, then the shared-memory / L2-slot kernel for the rest.
+    Pass regp[kMaxClasses];
+    int nreg = 0;
+    bool covered = false;
+    int order[16], cnt = 0;
+    for (int i = 0; i < reg_count() && cnt < 16; ++i) {
+      int mm, nn, ww;
+      reg_limits(i, &mm, &nn, &ww);
+      if (ww == want_w) order[cnt++] = i;
+    }
+    for (int a = 0; a < cnt; ++a)        // by capacity, smallest first
+      for (int c = a + 1; c < cnt; ++c) {
+        int ma, na, mc, nc, w0;
+        reg_limits(order[a], &ma, &na, &w0);
+        reg_limits(order[c], &mc, &nc, &w0);
+        if (mc * nc < ma * na) { const int t = order[a]; order[a] = order[c]; order[c] = t; }
+      }
+    for (int a = 0; a < cnt && !covered && nreg < kMaxClasses - 1; ++a) {
+      int mm, nn, ww;
+      reg_limits(order[a], &mm, &nn, &ww);
+      const int lm = mm < b->max_m ? mm : b->max_m, ln = nn < b->max_n ? nn : b->max_n;
+      if (nreg > 0 && lm <= pl->cls_m[nreg - 1] && ln <= pl->cls_n[nreg - 1]) continue;
+      Pass p;
+      if (reg_pass(d, b, order[a], lm, ln, mode, &p) != LPB_OK) continue;
+      p.list = LIST_CLASS;
+      p.cls = nreg;
+      pl->cls_m[nreg] = lm;
+      pl->cls_n[nreg] = ln;
+      regp[nreg++] = p;
+      covered = lm >= b->max_m && ln >= b->max_n;
+    }
+    if (nreg > 0) {
+      pl->classes = true;
+      pl->nclass = nreg + (covered ? 0 : 1);
+      if (!covered) {              // the largest LPs first: the tableau kernel's class
+        Pass &p = pl->pass[np];
+        if ((e = make_pass(d, b, &og, false, 0, mode, &p)) != LPB_OK) return e;
+        p.list = LIST_CLASS;
+        p.cls = nreg;
+        p.lim_m = b->max_m;
+        p.lim_n = b->max_n;
+        pl->cls_m[nreg] = b->max_m;
+        pl->cls_n[nreg] = b->max_n;
+        ++np;
+      }
+      for (int c = nreg - 1; c >= 0; --c) pl->pass[np++] = regp[c];
+    }
   }
-  if (o->kernel == LPB_KERNEL_REG && reg < 0) return LPB_EUNSUPPORTED;
-  if (reg >= 0) {   // pass 0: register-resident FP32 tableau
-    Pass &p0 = pl->pass[0];
-    p0.fp64 = false;
-    p0.mode = mode;
-    p0.reg = reg;
-    p0.threads = reg_threads;
-    p0.smem = reg_smem;
-    p0.grid = reg_occ * d.sms;
-    if (p0.grid > b->count) p0.grid = b->count > 0 ? b->count : 1;
-  } else if ((e = make_pass(d, b, o, !fp32, 0, mode, &pl->pass[0])) != LPB_OK) {
-    return e;
+  if (np == 0) {                   // one first pass over every LP
+    Pass &p = pl->pass[0];
+    const int reg = (fp32 && o->kernel == LPB_KERNEL_REG) ? reg_pick(b->max_m, b->max_n, want_w) : -1;
+    if (o->kernel == LPB_KERNEL_REG && reg < 0) return LPB_EUNSUPPORTED;
+    if (reg >= 0) {
+      if ((e = reg_pass(d, b, reg, b->max_m, b->max_n, mode, &p)) != LPB_OK) return e;
+    } else if ((e = make_pass(d, b, &og, !fp32, 0, mode, &p)) != LPB_OK) {
+      return e;
+    }
+    p.list = LIST_ALL;
+    p.lim_m = b->max_m;
+    p.lim_n = b->max_n;
+    np = 1;
   }
-  lpb_options o1 = *o;   // later passes run the shared-memory / L2-slot kernel
-  if (o1.kernel == LPB_KERNEL_REG) { o1.kernel = LPB_KERNEL_AUTO; o1.threads = 0; }
-  o = &o1;
-  if ((e = make_pass(d, b, o, !fp32, b->max_m, mode, &pl->pass[1])) != LPB_OK) return e;
-  pl->npass = 2;
+  {                                // LPs that need more artificial columns (Phase I)
+    Pass &p = pl->pass[np];
+    if ((e = make_pass(d, b, &og, !fp32, b->max_m, mode, &p)) != LPB_OK) return e;
+    p.list = LIST_DEFER;
+    p.group = 1;
+    p.lim_m = b->max_m;
+    p.lim_n = b->max_n;
+    ++np;
+  }
   pl->resolve = o->prec == LPB_FP32_REFINE;
-  if (pl->resolve) {
-    lpb_options o64 = *o;
-    if (o64.kernel == LPB_KERNEL_REG) o64.kernel = LPB_KERNEL_AUTO;
-    if ((e = make_pass(d, b, &o64, true, b->max_m, MODE_FP64, &pl->pass[2])) != LPB_OK) return e;
-    pl->npass = 3;
+  if (pl->resolve) {               // FP64 re-solve of the LPs that failed the FP32 certificate
+    Pass &p = pl->pass[np];
+    if ((e = make_pass(d, b, &og, true, b->max_m, MODE_FP64, &p)) != LPB_OK) return e;
+    p.list = LIST_RESOLVE;
+    p.group = 2;
+    p.lim_m = b->max_m;
+    p.lim_n = b->max_n;
+    ++np;
   }
+  pl->npass = np;
   pl->own_basis = pl->resolve && !basis_given;
   size_t off = 0;
   const size_t cnt = size_t(b->count > 0 ? b->count : 1);
   pl->off_defer = off;   off = align256(off + cnt * 4);
   pl->off_resolve = off; off = align256(off + cnt * 4);
   pl->off_basis = off;   off = align256(off + (pl->own_basis ? cnt * size_t(b->max_m) * 4 : 0));
+  pl->off_lists = off;   off = align256(off + (pl->classes ? cnt * size_t(pl->nclass) * 4 : 0));
+  pl->off_hist = off;    off = align256(off + (pl->classes ? classify_hist_bytes(pl->nclass) : 0));
+  pl->off_cctr = off;    off = align256(off + (kMaxPasses + kMaxClasses) * sizeof(int32_t));
   pl->off_slots = off;
   size_t slots = 0;
   for (int i = 0; i < pl->npass; ++i)
     if (pl->pass[i].gmem) {
-      const size_t s = size_t(pl->pass[i].grid) * pl->pass[i].slot_bytes;
-      if (s > slots) slots = s;
+      const size_t sz = size_t(pl->pass[i].grid) * pl->pass[i].slot_bytes;
+      if (sz > slots) slots = sz;
     }
   pl->total = align256(off + slots);
   return LPB_OK;
@@ -217,33 +300,62 @@ lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_ba
   if (ws_bytes < pl.total || (pl.total > 0 && !ws)) return LPB_ENOMEM;
   if (reinterpret_cast<uintptr_t>(ws) & 255) return LPB_EINVAL;
   unsigned char *w = static_cast<unsigned char *>(ws);
+  int32_t *queues = reinterpret_cast<int32_t *>(w + pl.off_cctr);   // one per pass
+  int32_t *class_count = queues + kMaxPasses;
   if (cudaMemsetAsync(ctr, 0, kCounters * sizeof(int32_t), s) != cudaSuccess) return LPB_ECUDA;
+  if (cudaMemsetAsync(queues, 0, (kMaxPasses + kMaxClasses) * sizeof(int32_t), s) != cudaSuccess) return LPB_ECUDA;
+  int group = -1;
   for (int i = 0; i < pl.npass; ++i) {
     const Pass &ps = pl.pass[i];
-    cudaEvent_t *ev = prof_ev ? prof_ev + i * 2 : nullptr;
-    if (ev && cudaEventRecord(ev[0], s) != cudaSuccess) return LPB_ECUDA;
+    if (ps.group != group) {     // timing: one event pair around each group of passes
+      if (prof_ev && group >= 0 && cudaEventRecord(prof_ev[group * 2 + 1], s) != cudaSuccess) return LPB_ECUDA;
+      group = ps.group;
+      if (prof_ev) {
+        if (cudaEventRecord(prof_ev[group * 2], s) != cudaSuccess) return LPB_ECUDA;
+        prof_ran[group] = true;
+      }
+      if (group == 0 && pl.classes) {
+        ClassPlanParams cp{};
+        cp.count = b->count;
+        cp.nclass = pl.nclass;
+        cp.m = b->m;
+        cp.n = b->n;
+        for (int c = 0; c < pl.nclass; ++c) { cp.max_m[c] = pl.cls_m[c]; cp.max_n[c] = pl.cls_n[c]; }
+        cp.hist = reinterpret_cast<int32_t *>(w + pl.off_hist);
+        cp.lists = reinterpret_cast<int32_t *>(w + pl.off_lists);
+        cp.class_count = class_count;
+        if (launch_classify(cp, d.sms, s) != cudaSuccess) return LPB_ECUDA;
+      }
+    }
     TableauParams p = base_params(ctr, err, b, r, o, pl, w);
     p.kcap = ps.kcap;
     p.mode = ps.mode;
     p.slot_bytes = ps.slot_bytes;
-    p.queue = ctr + (i == 0 ? CTR_Q1 : i == 1 ? CTR_Q2 : CTR_Q3);
-    if (i == 0) {
-      p.in = WorkList{nullptr, nullptr};
-    } else if (i == 1) {
-      p.in = WorkList{p.defer_items, p.defer_count};
-      p.defer_items = nullptr;   // kcap = max_m: nothing is deferred again
-    } else {
-      p.in = WorkList{p.resolve_items, p.resolve_count};
-      p.warm = 1;
+    p.lim_m = ps.lim_m;
+    p.lim_n = ps.lim_n;
+    p.queue = queues + i;
+    switch (ps.list) {
+      case LIST_ALL:
+        p.in = WorkList{nullptr, nullptr};
+        break;
+      case LIST_CLASS:
+        p.in = WorkList{reinterpret_cast<int32_t *>(w + pl.off_lists) + size_t(ps.cls) * size_t(b->count),
+                        class_count + ps.cls};
+        break;
+      case LIST_DEFER:
+        p.in = WorkList{p.defer_items, p.defer_count};
+        p.defer_items = nullptr;   // kcap = max_m: nothing is deferred again
+        break;
+      default:
+        p.in = WorkList{p.resolve_items, p.resolve_count};
+        p.warm = 1;
+        break;
     }
     const cudaError_t ce = ps.reg >= 0 ? launch_reg(p, ps.reg, ps.grid, ps.smem, s)
                                        : launch_tableau(p, ps.fp64, ps.gmem, ps.grid, ps.threads, ps.smem, s);
     if (ce != cudaSuccess) return LPB_ECUDA;
-    if (ev) {
-      if (cudaEventRecord(ev[1], s) != cudaSuccess) return LPB_ECUDA;
-      prof_ran[i] = true;
-    }
   }
+  if (prof_ev && group >= 0 && cudaEventRecord(prof_ev[group * 2 + 1], s) != cudaSuccess) return LPB_ECUDA;
   return LPB_OK;
 }
 

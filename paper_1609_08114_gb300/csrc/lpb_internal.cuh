@@ -177,6 +177,7 @@ struct TableauParams {
   int warm;                    // start from the basis in bbuf (FP64 re-solve)
   void *slots;                 // GMEM class: per-CTA tableau slots
   size_t slot_bytes;
+  int lim_m, lim_n;            // size bounds of this launch (register kernel: its class)
   int kcap;                    // artificial columns this launch can hold
   int mode;                    // Mode
   int max_iter;                // 0: 50 (m + n)
@@ -196,6 +197,19 @@ struct BackwardParams {
   uint32_t *err;
 };
 
+// Size classes of a mixed batch (plan.cu).  Class c < nclass - 1 takes the LPs
+// with m <= max_m[c] and n <= max_n[c] not taken by an earlier class; the last
+// class takes the rest.  lists holds nclass lists of `count` slots each.
+constexpr int kMaxClasses = 8;
+struct ClassPlanParams {
+  int count, nclass;
+  const int32_t *m, *n;
+  int max_m[kMaxClasses], max_n[kMaxClasses];
+  int32_t *hist;          // nclass * 64 cost-bucket counters (scratch)
+  int32_t *lists;         // class c's LPs at lists[c * count ...], largest cost first
+  int32_t *class_count;   // nclass list lengths
+};
+
 struct HyperboxParams {
   int64_t count;
   int n, dtype, shared_box;
@@ -213,7 +227,11 @@ cudaError_t launch_tableau(const TableauParams &p, bool fp64, bool gmem, int gri
 // Register-resident FP32 kernel (simplex_reg.cu): configuration index for
 // (max_m, max_n) or -1, its occupancy, and its launch.  It defers to the
 // defer list every LP it does not take (Phase I, sizes, non-finite data).
+size_t classify_hist_bytes(int nclass);
+cudaError_t launch_classify(const ClassPlanParams &p, int sms, cudaStream_t s);
 int reg_pick(int max_m, int max_n, int want_warps);
+int reg_count();
+void reg_limits(int cfg, int *max_m, int *max_n, int *warps);
 cudaError_t reg_occupancy(int cfg, int max_m, int max_n, int dtype, int *ctas, int *threads, size_t *smem);
 cudaError_t launch_reg(const TableauParams &p, int cfg, int grid, size_t smem, cudaStream_t s);
 size_t hyperbox_smem_bytes(int n, int elem_bytes, bool shared_box);

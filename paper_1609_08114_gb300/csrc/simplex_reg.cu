@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauPa
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const float eps_p = float(P.eps_p), eps_d = float(P.eps_d);
   const int dt = P.B.dtype;
-  const int sld = a_stride(P.B.max_n);
+  const int sld = a_stride(P.lim_n);
   const int nitems = P.in.count ? min(*P.in.count, P.list_cap) : P.B.count;
   float T[R][C];
 
@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauPa
     const int m = P.B.m[lp], n = P.B.n[lp];
     const int64_t aoff = P.B.a_off[lp], boff = P.B.b_off[lp], coff = P.B.c_off[lp];
     // ---- admission: sizes that fit the template, b >= 0, finite b and c ----
-    const bool fits = m >= 1 && n >= 1 && m <= ROWS - 1 && n <= COLS - 1 && m <= P.B.max_m && n <= P.B.max_n;
+    const bool fits = m >= 1 && n >= 1 && m <= ROWS - 1 && n <= COLS - 1 && m <= P.B.max_m && n <= P.B.max_n &&
+                      m <= P.lim_m && n <= P.lim_n;
     if (fits) {    // start streaming A now; its copies land while b and c are checked
       if (dt == LPB_DTYPE_F64) {
         const double *A = static_cast<const double *>(P.B.A) + aoff;
@@ -586,6 +587,16 @@ size_t reg_smem_bytes(int cfg, int max_m, int max_n, int dtype) {
 }
 
 }  // namespace
+
+int reg_count() { return kNumReg; }
+
+// Largest m and n configuration `cfg` holds, and its warps per CTA.
+void reg_limits(int cfg, int *max_m, int *max_n, int *warps) {
+  const RegConfig &k = kRegConfigs[cfg];
+  *max_m = 32 * k.R - 1;
+  *max_n = k.W * k.C - 1;
+  *warps = k.W;
+}
 
 // Smallest configuration whose rows hold max_m + 1 and columns max_n + 1,
 // with `want_w` warps when given (8 warps by default); -1 if none fits.

@@ -163,3 +163,39 @@ def test_full_size_sampled_parity(solver):
         sel["y"] = np.concatenate([got["y"][sb.b_off[k]:sb.b_off[k] + 100] for k in idx])
         sel["basis"] = np.concatenate([got["basis"][sb.b_off[k]:sb.b_off[k] + 100] for k in idx])
         compare(sub, sel, obj_rtol=rtol)
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp32_refine", 1e-8), ("fp64", 1e-9)])
+def test_mixed_sizes_up_to_256(solver, prec, rtol):
+    """The mixed-size workload's distribution (m, n ~ U{8..256}): the batch is split into size
+    classes (register templates and the tableau kernel for the rest)."""
+    sb = synth.mixed_sizes(20000, seed=4, first=0, stop=160)
+    got = run(solver, sb, prec)
+    compare(sb, got, obj_rtol=rtol)
+
+
+def test_cuda_graph_replay_matches_eager(solver):
+    """A whole solve is a fixed sequence of memsets and kernels with device-side work-list
+    lengths, so it can be captured once and replayed."""
+    sb = synth.mixed_sizes(300, seed=12, lo=4, hi=150)
+    dev = to_device(sb)
+    eager = host(solver.solve(dev, prec="fp32_refine"))
+    out = solver.alloc_result(dev)
+    solver.solve(dev, prec="fp32_refine", out=out)          # sizes the workspace before capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            solver.solve(dev, prec="fp32_refine", out=out)
+    for t in (out.status, out.iters):
+        t.fill_(-9)
+    out.obj.fill_(float("nan"))
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    rep = host(out)
+    assert np.array_equal(rep["status"], eager["status"])
+    assert np.array_equal(rep["obj"], eager["obj"])
+    assert np.array_equal(rep["x"], eager["x"])
