@@ -105,8 +105,8 @@ typedef struct {
   double feas_tol;           /* Phase I / verification tolerance [1e-9] */
   int32_t keep_basis_inverse;/* keep what lpb_solve_backward needs in ws [0] */
   int32_t kernel;            /* lpb_kernel: force a kernel class [LPB_KERNEL_AUTO] */
-  int32_t threads;           /* threads per CTA for the tableau kernel, 0 = auto */
-  int32_t reserved;
+  int32_t threads;           /* threads per CTA of the tableau kernel [auto] */
+  int32_t reg_warps;         /* warps per LP of the register kernel, 4 or 8 [autotuned, else 8] */
 } lpb_options;
 
 typedef enum {
@@ -155,6 +155,21 @@ lpb_err lpb_solve_backward(lpb_handle *handle, const lpb_batch *batch, const lpb
 lpb_err lpb_hyperbox(lpb_handle *handle, int64_t count, int32_t n, int32_t dtype,
                      const void *c, const void *l, const void *u, int32_t shared_box,
                      void *obj, void *x, void *stream);
+
+/* Autotuner.  Picks, for batches shaped like `batch` (same max_m, max_n,
+ * dtype and precision), the fastest schedule among: warps per LP of the
+ * register kernel (4 or 8), threads per CTA of the tableau kernel (128 or
+ * 256) and its placement (shared memory when it fits, or L2-resident slots).
+ * If `table_path` (may be NULL) holds an entry for this shape, that entry is
+ * loaded and nothing is timed; otherwise every candidate solves `batch` into
+ * `result` on `stream` (one warm-up and two timed runs each, CUDA events),
+ * the winner is stored in the handle and appended to `table_path`.  Later
+ * lpb_solve calls whose options leave kernel, threads and reg_warps at 0 use
+ * the tuned schedule.  Synchronises `stream`.  *best_ms (nullable) receives
+ * the winner's time per solve (0 when loaded from the table). */
+lpb_err lpb_autotune(lpb_handle *handle, const lpb_batch *batch, const lpb_options *opt,
+                     const lpb_result *result, void *ws, size_t ws_bytes, const char *table_path,
+                     void *stream, float *best_ms);
 
 /* Synchronise `stream`, read and clear the device error word.  Returns
  * LPB_OK or LPB_EDEVICE (word != 0; *word receives it when non-NULL). */

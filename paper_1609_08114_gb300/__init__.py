@@ -129,10 +129,10 @@ class Solver:
     # -- options / workspace ------------------------------------------------
     @staticmethod
     def options(prec="fp32_refine", max_iter=0, eps_p=0.0, eps_d=0.0, feas_tol=0.0, kernel=KERNEL_AUTO,
-                threads=0, keep_basis_inverse=0) -> _lib.Options:
+                threads=0, keep_basis_inverse=0, reg_warps=0) -> _lib.Options:
         p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
         return _lib.Options(p, int(max_iter), float(eps_p), float(eps_d), float(feas_tol),
-                            int(keep_basis_inverse), int(kernel), int(threads), 0)
+                            int(keep_basis_inverse), int(kernel), int(threads), int(reg_warps))
 
     def workspace_size(self, batch: LPBatch, opt: _lib.Options) -> int:
         n = ctypes.c_size_t()
@@ -165,6 +165,21 @@ class Solver:
         _lib.check(self.lib.lpb_solve(self.h, ctypes.byref(cb), ctypes.byref(opt), ctypes.byref(cr),
                                       _ptr(ws), ws.numel(), _stream_handle(self.device)), "lpb_solve")
         return res
+
+    def autotune(self, batch: LPBatch, prec="fp32_refine", table_path: str | None = None,
+                 out: SolveResult | None = None, **kw) -> float:
+        """Pick the fastest schedule for batches shaped like ``batch`` (lpb_autotune); later solves
+        with default options use it.  Returns the winner's ms per solve (0 if loaded from the table)."""
+        opt = self.options(prec, **kw)
+        res = out if out is not None else self.alloc_result(batch)
+        ws = self.workspace(self.workspace_size(batch, opt))
+        cb, cr = batch.cstruct(), res.cstruct()
+        ms = ctypes.c_float()
+        path = None if table_path is None else str(table_path).encode()
+        _lib.check(self.lib.lpb_autotune(self.h, ctypes.byref(cb), ctypes.byref(opt), ctypes.byref(cr), _ptr(ws),
+                                         ws.numel(), path, _stream_handle(self.device), ctypes.byref(ms)),
+                   "lpb_autotune")
+        return float(ms.value)
 
     def solve_backward(self, batch: LPBatch, res: SolveResult, g_obj: torch.Tensor | None,
                        g_x: torch.Tensor | None):

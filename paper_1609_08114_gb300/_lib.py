@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("eps_p", ctypes.c_double),
                 ("eps_d", ctypes.c_double), ("feas_tol", ctypes.c_double),
                 ("keep_basis_inverse", ctypes.c_int32), ("kernel", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("reg_warps", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -60,6 +60,8 @@ SIGNATURES = {
                                           ctypes.POINTER(Result), P, P, P, P, P, P, ctypes.c_size_t, P]),
     "lpb_hyperbox": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P, P,
                                     ctypes.c_int32, P, P, P]),
+    "lpb_autotune": (ctypes.c_int, [P, ctypes.POINTER(Batch), ctypes.POINTER(Options), ctypes.POINTER(Result), P,
+                                    ctypes.c_size_t, ctypes.c_char_p, P, ctypes.POINTER(ctypes.c_float)]),
     "lpb_sync_error": (ctypes.c_int, [P, P, ctypes.POINTER(ctypes.c_uint32)]),
     "lpb_get_stats": (ctypes.c_int, [P, P, ctypes.POINTER(Stats)]),
     "lpb_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(Batch), ctypes.POINTER(Options), ctypes.POINTER(Result),

@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "lpb_internal.cuh"
 
@@ -23,6 +24,12 @@ struct lpb_handle {
   cudaEvent_t *prof_ev = nullptr;   // [kProfMax * 3 * 2]
   bool prof_ran[kProfMax * 3] = {};
   int prof_cap = 0, prof_n = 0;
+  // Autotuned schedules (lpb_autotune), by batch shape.
+  struct Tuned {
+    int max_m, max_n, dtype, prec;
+    int kernel, threads, reg_warps;
+  };
+  std::vector<Tuned> tuned;
 };
 
 namespace {
@@ -146,7 +153,8 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   pl->feas_tol = o->feas_tol > 0 ? o->feas_tol : 1e-9;
   lpb_err e;
   const int mode = o->prec == LPB_FP64 ? MODE_FP64 : o->prec == LPB_FP32 ? MODE_FP32 : MODE_FP32_REFINE;
-  const int want_w = o->threads > 0 ? o->threads / 32 : 8;
+  const int want_w = o->reg_warps > 0 ? o->reg_warps
+                   : (o->kernel == LPB_KERNEL_REG && o->threads > 0) ? o->threads / 32 : 8;
   lpb_options og = *o;          // options of the shared-memory / L2-slot kernel passes
   if (og.kernel == LPB_KERNEL_REG) { og.kernel = LPB_KERNEL_AUTO; og.threads = 0; }
   int np = 0;
@@ -447,6 +455,17 @@ lpb_err lpb_solve(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const
   if (!r->status || !r->obj || !r->x) return LPB_EINVAL;
   DeviceScope ds(h->device);
   if (!ds.ok()) return LPB_ECUDA;
+  lpb_options tuned_opt;
+  if (o->kernel == LPB_KERNEL_AUTO && o->threads == 0 && o->reg_warps == 0)
+    for (const auto &t : h->tuned)
+      if (t.max_m == b->max_m && t.max_n == b->max_n && t.dtype == b->dtype && t.prec == o->prec) {
+        tuned_opt = *o;
+        tuned_opt.kernel = t.kernel;
+        tuned_opt.threads = t.threads;
+        tuned_opt.reg_warps = t.reg_warps;
+        o = &tuned_opt;
+        break;
+      }
   const bool prof = h->prof_ev && h->prof_n < h->prof_cap;
   const lpb_err e = run_solve(device_info(h), h->d_ctr, h->d_err, b, o, r, ws, ws_bytes,
                               static_cast<cudaStream_t>(stream),
@@ -454,6 +473,87 @@ lpb_err lpb_solve(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const
                               prof ? h->prof_ran + h->prof_n * 3 : nullptr);
   if (e == LPB_OK && prof) ++h->prof_n;
   return e;
+}
+
+lpb_err lpb_autotune(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const lpb_result *r,
+                     void *ws, size_t ws_bytes, const char *table_path, void *stream, float *best_ms) {
+  if (!h || !b || !o || !r) return LPB_EINVAL;
+  if (best_ms) *best_ms = 0.f;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  lpb_handle::Tuned key{b->max_m, b->max_n, b->dtype, o->prec, 0, 0, 0};
+  auto store = [&](const lpb_handle::Tuned &t) {
+    for (auto &e : h->tuned)
+      if (e.max_m == t.max_m && e.max_n == t.max_n && e.dtype == t.dtype && e.prec == t.prec) { e = t; return; }
+    h->tuned.push_back(t);
+  };
+  if (table_path) {                     // a stored entry for this shape wins
+    if (FILE *f = std::fopen(table_path, "r")) {
+      char tag[16];
+      lpb_handle::Tuned t{};
+      float ms = 0.f;
+      bool found = false;
+      while (std::fscanf(f, "%15s %d %d %d %d %d %d %d %f", tag, &t.max_m, &t.max_n, &t.dtype, &t.prec, &t.kernel,
+                         &t.threads, &t.reg_warps, &ms) == 9)
+        if (!std::strcmp(tag, "lpb-tune") && t.max_m == key.max_m && t.max_n == key.max_n &&
+            t.dtype == key.dtype && t.prec == key.prec) {
+          store(t);
+          found = true;
+        }
+      std::fclose(f);
+      if (found) return LPB_OK;
+    }
+  }
+  if (b->count <= 0) return LPB_EINVAL;
+  struct Cand { int kernel, threads, reg_warps; };
+  const bool fp32 = o->prec != LPB_FP64;
+  const Cand cands[] = {
+      {LPB_KERNEL_AUTO, 0, fp32 ? 8 : 0}, {LPB_KERNEL_AUTO, 0, fp32 ? 4 : 0}, {LPB_KERNEL_AUTO, 128, fp32 ? 8 : 0},
+      {LPB_KERNEL_AUTO, 256, fp32 ? 8 : 0}, {LPB_KERNEL_SMEM, 0, 0}, {LPB_KERNEL_GMEM, 0, 0}};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return LPB_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return LPB_ECUDA; }
+  const DeviceInfo d = device_info(h);
+  float best = -1.f;
+  lpb_handle::Tuned win = key;
+  lpb_err status = LPB_OK;
+  for (const Cand &c : cands) {
+    lpb_options oc = *o;
+    oc.kernel = c.kernel;
+    oc.threads = c.threads;
+    oc.reg_warps = c.reg_warps;
+    size_t need = 0;
+    if (solve_workspace_bytes(d, b, &oc, r->basis != nullptr, &need) != LPB_OK || need > ws_bytes) continue;
+    if (run_solve(d, h->d_ctr, h->d_err, b, &oc, r, ws, ws_bytes, s, nullptr, nullptr) != LPB_OK) continue;
+    if (cudaEventRecord(e0, s) != cudaSuccess) { status = LPB_ECUDA; break; }
+    lpb_err er = LPB_OK;
+    for (int rep = 0; rep < 2 && er == LPB_OK; ++rep)
+      er = run_solve(d, h->d_ctr, h->d_err, b, &oc, r, ws, ws_bytes, s, nullptr, nullptr);
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { status = LPB_ECUDA; break; }
+    float ms = 0.f;
+    if (er != LPB_OK || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
+    ms *= 0.5f;
+    if (best < 0.f || ms < best) {
+      best = ms;
+      win.kernel = c.kernel;
+      win.threads = c.threads;
+      win.reg_warps = c.reg_warps;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != LPB_OK) return status;
+  if (best < 0.f) return LPB_EUNSUPPORTED;
+  store(win);
+  if (best_ms) *best_ms = best;
+  if (table_path)
+    if (FILE *f = std::fopen(table_path, "a")) {
+      std::fprintf(f, "lpb-tune %d %d %d %d %d %d %d %.6f\n", win.max_m, win.max_n, win.dtype, win.prec, win.kernel,
+                   win.threads, win.reg_warps, best);
+      std::fclose(f);
+    }
+  return LPB_OK;
 }
 
 lpb_err lpb_profile_start(lpb_handle *h, int32_t calls) {
