@@ -1,19 +1,26 @@
 """Benchmark: LPs/s of the batched simplex at m = n = 100 (FP32 tableau + FP64 refinement,
 beside the plain FP64 tableau), on one batch of 50,000 type-1 LPs per GPU.
 
-One step = one lpb_solve over the whole resident batch (load, Phase I check,
-pivots, FP64 refinement and verification, FP64 re-solve of failures, outputs).
-Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle instead.
+One step = one lpb_solve over the whole resident batch: size classes, pivots, FP64
+refinement and KKT certificate, FP64 re-solve of failures, outputs.  Prints one JSON line
+(rank 0).  ``--impl reference`` times the CPU oracle on samples of the same workload.
+
+Secondary legs (skip with ``--no-legs``) time the other workloads once each with CUDA
+events: 1,000 x m=n=16; the m=n sweep; 10,000 x m=n=200 two-phase; hyperbox support
+functions (4,000,000 x 5 FP32, 6,000,000 x 28 FP64); 20,000 mixed sizes forward and
+forward+backward.
 
 Launch: ``python bench.py --gpus 1 --steps K --warmup W``; for N > 1 under
-``torch.distributed.run`` (one rank per GPU; each rank solves its own 50,000 LPs,
-weak scaling, no data-path collective).
+``torch.distributed.run`` (one rank per GPU; each rank solves its own 50,000 LPs, weak
+scaling, no data-path collective).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -27,13 +34,15 @@ sys.path.insert(0, ROOT)
 COUNT, M, N, SEED = 50_000, 100, 100, 1
 METRIC = "LPs/sec at m=n=100 (FP32+FP64-refine vs plain FP64, rel obj err<=1e-8)"
 WORKLOAD = "type-1 LPs, 50,000 per GPU, m=n=100, A~U[0.1,1], b~U[1,10], c~U[0,1], seed 1"
+FP32_FMA_PIPES_PER_SM = 128
+SMS = 152
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="lpb", choices=["lpb", "reference"])
     ap.add_argument("--count", type=int, default=COUNT)
     ap.add_argument("--no-legs", action="store_true", help="skip the secondary workloads")
@@ -42,10 +51,12 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def rank_range(rank: int, count: int):
+    """LPs of rank `rank`: its own block of `count` LPs of one seeded stream (weak scaling)."""
+    return count * rank, count * (rank + 1)
 
 
 class ClockSampler:
@@ -56,9 +67,7 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
-        self.idx = gpu_index
-        self.proc = None
-        self.f = None
+        self.idx, self.proc, self.f = gpu_index, None, None
 
     def __enter__(self):
         try:
@@ -66,6 +75,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
         except Exception:
             self.proc = None
         return self
@@ -80,38 +90,47 @@ class ClockSampler:
 
     def summary(self):
         if self.proc is None or self.f is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         self.f.flush()
         rows = [r.split(", ") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
         os.unlink(self.f.name)
         rows = [r for r in rows if len(r) >= 9]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        num = lambda x: float(x) if re.fullmatch(r"[0-9.]+", x.strip()) else None
+        sm = [v for v in (num(r[1]) for r in rows) if v is not None]
+        mx = [v for v in (num(r[2]) for r in rows) if v is not None]
+        pw = [v for v in (num(r[3]) for r in rows) if v is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "power_w_max": max(pw) if pw else None, "reasons": reasons, "samples": len(rows)}
 
 
-def make_batch(rank: int, count: int):
-    import synth
-    return synth.type1(count * (rank + 1), M, N, seed=SEED, first=count * rank, stop=count * (rank + 1))
+def profiled_traffic():
+    """DRAM bytes per launch of the register kernel from the committed ncu summary, if the
+    kernel source is unchanged since that capture (else None)."""
+    try:
+        txt = open(os.path.join(ROOT, "profiles", "reg_kernel_type1_m100.md")).read()
+        want = re.search(r"source-sha256-16:\s*([0-9a-f]{16})", txt).group(1)
+        per = float(re.search(r"dram_bytes_per_launch_50000:\s*([0-9.e+]+)", txt).group(1))
+        src = open(os.path.join(ROOT, "paper_1609_08114_gb300", "csrc", "simplex_reg.cu"), "rb").read()
+        return per if hashlib.sha256(src).hexdigest()[:16] == want else None
+    except Exception:
+        return None
 
 
-def algorithmic_flops(iters: np.ndarray) -> float:
+def algorithmic_flops(iters: np.ndarray, m: int, n: int) -> float:
     """2 (m+1)(n+1) flops per pivot of the compact tableau, times the pivots taken."""
-    return float(iters.astype(np.float64).sum()) * 2.0 * (M + 1) * (N + 1)
+    return float(iters.astype(np.float64).sum()) * 2.0 * (m + 1) * (n + 1)
 
 
-def algorithmic_bytes(count: int, in_bytes: int) -> float:
+def algorithmic_bytes(count: int, m: int, n: int, in_bytes: int) -> float:
     """Per LP: read A, b, c once; write x, y, obj (FP64), status, iters and the basis."""
-    per = (M * N + M + N) * in_bytes + (N + M + 1) * 8 + 4 * (M + 2)
-    return float(per) * count
+    return float((m * n + m + n) * in_bytes + (n + m + 1) * 8 + 4 * (m + 2)) * count
 
 
-def cpu_baseline(sb, budget_s: float = 20.0):
+def cpu_baseline(sb, budget_s: float = 15.0):
     import oracle
     threads = oracle.max_threads()
     sample = sb.subset(np.arange(min(2000, sb.count)))
@@ -133,22 +152,25 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    sb = make_batch(0, args.count)
+    import synth
     threads = oracle.max_threads()
-    per = 10_000 if args.count >= 10_000 else args.count
+    per = min(10_000, args.count)
     times = []
     for step in range(args.warmup + args.steps):
-        lo = (step * per) % sb.count
-        sample = sb.subset(np.arange(lo, min(lo + per, sb.count)))
+        lo = (step * per) % args.count
+        sample = synth.type1(args.count, M, N, seed=SEED, first=lo, stop=min(lo + per, args.count))
         t0 = time.perf_counter()
         oracle.solve_batch(sample, nthreads=threads)
         if step >= args.warmup:
             times.append((time.perf_counter() - t0, sample.count))
-    tot_t = sum(t for t, _ in times); tot_n = sum(n for _, n in times)
+        if step >= args.warmup and sum(t for t, _ in times) > 120:
+            break
+    tot_t = sum(t for t, _ in times)
+    tot_n = sum(n for _, n in times)
     v = tot_n / tot_t
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "LPs/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(times),
+        "steps": len(times), "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample_per_step": per},
         "cpu_baseline": {"value": v, "unit": "LPs/s", "cores": threads, "kind": "oracle",
@@ -182,37 +204,43 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    import synth
     from paper_1609_08114_gb300 import LPBatch, Solver
 
-    sb = make_batch(rank, args.count)
+    lo, hi = rank_range(rank, args.count)
+    sb = synth.type1(hi, M, N, seed=SEED, first=lo, stop=hi)
     batch = LPBatch.from_packed(sb.m, sb.n, sb.A, sb.b, sb.c, device=dev, dtype=torch.float64)
     solver = Solver(local)
     res = solver.alloc_result(batch)
     stream = torch.cuda.current_stream(dev)
 
-    def timed(prec, steps, warmup, profile=False):
+    def timed(prec, steps, warmup, profile=False, clocks=False):
         for _ in range(warmup):
             solver.solve(batch, prec=prec, out=res)
         torch.cuda.synchronize(dev)
         barrier()
         torch.cuda.synchronize(dev)
         if profile:
-            solver.profile_start(steps)
-        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            solver.profile_start(min(steps, 256))
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
             solver.solve(batch, prec=prec, out=res)
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.__exit__(None, None, None)
         barrier()
         ms = e0.elapsed_time(e1) / steps
-        prof = solver.profile_read(steps) if profile else None
-        return max_over_ranks(ms), prof
+        prof = solver.profile_read(min(steps, 256)) if profile else None
+        return max_over_ranks(ms), prof, (sampler.summary() if sampler else None)
 
-    # headline: FP32 tableau + FP64 refinement
-    with ClockSampler(local) as clk:
-        ms, prof = timed("fp32_refine", args.steps, max(args.warmup, 3), profile=True)
-    clocks = clk.summary()
+    warmup = max(args.warmup, 3)
+    ms, prof, clocks = timed("fp32_refine", args.steps, warmup, profile=True, clocks=True)
     stats = solver.stats()
     iters = res.iters.cpu().numpy()
     status = res.status.cpu().numpy()
@@ -222,39 +250,42 @@ def main():
     import oracle
     idx = np.unique(np.linspace(0, sb.count - 1, 200).astype(int))
     ref = oracle.solve_batch(sb.subset(idx))
-    objg = res.obj.cpu().numpy()[idx]
-    relerr = float(np.max(np.abs(objg - ref["obj"]) / (1 + np.abs(ref["obj"]))))
+    relerr = float(np.max(np.abs(res.obj.cpu().numpy()[idx] - ref["obj"]) / (1 + np.abs(ref["obj"]))))
 
     # plain FP64 on the same batch
-    ms64, prof64 = timed("fp64", max(2, args.steps // 2), 2, profile=True)
+    ms64, prof64, _ = timed("fp64", max(3, args.steps // 10), 2, profile=True)
     iters64 = res.iters.cpu().numpy()
-    objg64 = res.obj.cpu().numpy()[idx]
-    relerr64 = float(np.max(np.abs(objg64 - ref["obj"]) / (1 + np.abs(ref["obj"]))))
+    relerr64 = float(np.max(np.abs(res.obj.cpu().numpy()[idx] - ref["obj"]) / (1 + np.abs(ref["obj"]))))
 
     # end to end through the public API: pinned host inputs in, objective out
     hA = batch.A.cpu().pin_memory(); hb = batch.b.cpu().pin_memory(); hc = batch.c.cpu().pin_memory()
     hobj = torch.empty(batch.count, dtype=torch.float64).pin_memory()
-    h2d = hA.numel() * 8 + hb.numel() * 8 + hc.numel() * 8
+    h2d = (hA.numel() + hb.numel() + hc.numel()) * 8
     d2h = hobj.numel() * 8
 
     def e2e_step():
-        batch.A.copy_(hA, non_blocking=True); batch.b.copy_(hb, non_blocking=True)
+        batch.A.copy_(hA, non_blocking=True)
+        batch.b.copy_(hb, non_blocking=True)
         batch.c.copy_(hc, non_blocking=True)
         solver.solve(batch, prec="fp32_refine", out=res)
         hobj.copy_(res.obj, non_blocking=True)
 
     for _ in range(2):
         e2e_step()
-    torch.cuda.synchronize(dev); barrier()
-    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    steps_e2e = max(3, args.steps // 10)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps_e2e):
         e2e_step()
     e1.record(stream)
-    torch.cuda.synchronize(dev); barrier()
-    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / steps_e2e)
 
-    # roofline of the dominant kernel (pass 0: the FP32 tableau kernel over all LPs)
+    # roofline of the dominant kernel: the register-tableau launch (timing group 0)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -262,42 +293,46 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FP32 FMA pipes
+    fp32_peak = SMS * FP32_FMA_PIPES_PER_SM * 2 * sm_max * 1e6 / 1e12
     k_ms = float(np.mean(prof[:, 0])) if prof is not None and len(prof) else ms
-    flops = algorithmic_flops(iters)
-    achieved_alu = flops / (k_ms * 1e-3) / 1e12
-    achieved_hbm = algorithmic_bytes(args.count, 8) / (k_ms * 1e-3) / 1e9
+    traffic = profiled_traffic()
+    achieved_alu = algorithmic_flops(iters, M, N) / (k_ms * 1e-3) / 1e12
+    achieved_hbm = algorithmic_bytes(args.count, M, N, 8) / (k_ms * 1e-3) / 1e9
     roof_alu = {"bound": "alu", "achieved": achieved_alu, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved_alu / fp32_peak, "traffic": None}
+                "frac": achieved_alu / fp32_peak, "traffic": None,
+                "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x max SM clock"}
     roof_hbm = {"bound": "hbm", "achieved": achieved_hbm, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_hbm / hbm_peak, "traffic": None}
+                "frac": achieved_hbm / hbm_peak, "traffic": traffic, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     roofline = roof_hbm if roof_hbm["frac"] >= roof_alu["frac"] else roof_alu
 
     legs = {}
-    if not args.no_legs:
-        legs = secondary_legs(solver, dev, args)
+    if not args.no_legs and rank == 0:
+        legs = secondary_legs(solver, dev)
 
     out = {
         "metric": METRIC, "value": value, "unit": "LPs/s", "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "count_per_gpu": args.count, "m": M, "n": N, "input_dtype": "f64",
-                   "precision": "fp32 tableau + fp64 refine/verify + fp64 re-solve",
+                   "precision": "fp32 tableau + fp64 refine/certificate + fp64 re-solve",
                    "l2": "inputs (4 GB FP64 per GPU) exceed L2; no flush"},
-        "gpu_launches": int(args.steps * 3),
+        "gpu_launches": int(args.steps * stats["kernels"]),
         "clocks": clocks,
         "e2e": {"value": world * args.count / (ms_e2e * 1e-3), "unit": "LPs/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": roofline,
         "roofline_other": roof_alu if roofline is roof_hbm else roof_hbm,
-        "kernel_ms": {"fp32_pass0": k_ms, "fp32_pass1": float(np.mean(prof[:, 1])) if prof is not None else None,
-                      "fp64_resolve_pass2": float(np.mean(prof[:, 2])) if prof is not None else None},
-        "pivots_per_lp": float(iters.mean()), "resolved_fp64": stats["resolved_fp64"],
+        "kernel_ms": {"first_pass_group": k_ms,
+                      "phase1_pass": float(np.mean(prof[:, 1])) if prof is not None else None,
+                      "fp64_resolve_pass": float(np.mean(prof[:, 2])) if prof is not None else None},
+        "kernels_per_step": stats["kernels"], "pivots_per_lp": float(iters.mean()),
+        "resolved_fp64": stats["resolved_fp64"],
         "statuses": {str(k): int(v) for k, v in zip(*np.unique(status, return_counts=True))},
         "max_rel_obj_err_sample": relerr,
-        "fp64_plain": {"value": world * args.count / (ms64 * 1e-3), "ms_per_step": ms64,
+        "fp64_plain": {"value": world * args.count / (ms64 * 1e-3), "unit": "LPs/s", "ms_per_step": ms64,
                        "kernel_ms": float(np.mean(prof64[:, 0])) if prof64 is not None else None,
                        "pivots_per_lp": float(iters64.mean()), "max_rel_obj_err_sample": relerr64},
+        "speedup_fp32_refine_over_fp64": ms64 / ms,
         "legs": legs,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -308,34 +343,103 @@ def main():
         dist.destroy_process_group()
 
 
-def secondary_legs(solver, dev, args):
-    """Other workloads, timed with CUDA events after warm-up (LPs/s): hyperbox
-    (4M x n=5 FP32, 6M x n=28 FP64, per-LP boxes)."""
+def _time(fn, reps=5, warm=2):
     import torch
-    out = {}
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _type1_device(count, m, n, dev, seed):
+    import torch
+    from paper_1609_08114_gb300 import LPBatch
     g = torch.Generator(device=dev)
-    g.manual_seed(3)
+    g.manual_seed(seed)
+    A = 0.1 + 0.9 * torch.rand((count, m, n), generator=g, device=dev, dtype=torch.float64)
+    b = 1 + 9 * torch.rand((count, m), generator=g, device=dev, dtype=torch.float64)
+    c = torch.rand((count, n), generator=g, device=dev, dtype=torch.float64)
+    return LPBatch.from_dense(A, b, c)
+
+
+def secondary_legs(solver, dev):
+    """Each workload once (CUDA events after warm-up), LPs/s."""
+    import torch
+    import synth
+    from paper_1609_08114_gb300 import LPBatch, solve
+    out = {}
+
+    def solve_leg(name, batch, precs=("fp32_refine", "fp64"), reps=5):
+        res = solver.alloc_result(batch)
+        leg = {"count": batch.count}
+        for prec in precs:
+            ms = _time(lambda: solver.solve(batch, prec=prec, out=res), reps=reps)
+            st = res.status.cpu().numpy()
+            leg[prec] = {"LPs_per_s": batch.count / (ms * 1e-3), "ms": ms,
+                         "statuses": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
+                         "pivots_per_lp": float(res.iters.float().mean()), "resolved_fp64": solver.stats()["resolved_fp64"]}
+        out[name] = leg
+
+    # 1,000 x m=n=16 (FP64 input)
+    sb = synth.type1(1000, 16, 16, seed=0)
+    solve_leg("type1_1000x16", LPBatch.from_packed(sb.m, sb.n, sb.A, sb.b, sb.c, device=dev))
+    # the m=n sweep at 10,000 LPs (2,000 at 300)
+    for mn, cnt in ((5, 10_000), (28, 10_000), (50, 10_000), (200, 10_000), (300, 2_000)):
+        solve_leg(f"type1_{cnt}x{mn}", _type1_device(cnt, mn, mn, dev, seed=mn), reps=3)
+        torch.cuda.empty_cache()
+    # 10,000 x m=n=200 two-phase
+    sb = synth.type2(10_000, 200, 200, seed=2)
+    solve_leg("type2_10000x200", LPBatch.from_packed(sb.m, sb.n, sb.A, sb.b, sb.c, device=dev), reps=3)
+    del sb
+    torch.cuda.empty_cache()
+    # 20,000 mixed sizes, forward and forward + backward (autograd)
+    sb = synth.mixed_sizes(20_000, seed=4)
+    mix = LPBatch.from_packed(sb.m, sb.n, sb.A, sb.b, sb.c, device=dev)
+    solve_leg("mixed_20000_fwd", mix, precs=("fp32_refine",), reps=3)
+    A = mix.A.clone().requires_grad_(True)
+    b = mix.b.clone().requires_grad_(True)
+    c = mix.c.clone().requires_grad_(True)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    g_obj = torch.randn(mix.count, generator=g, device=dev, dtype=torch.float64)
+    g_x = torch.randn(mix.c.numel(), generator=g, device=dev, dtype=torch.float64)
+
+    def fwd_bwd():
+        obj, x, _, st = solve(A, b, c, mix.m, mix.n, prec="fp32_refine", solver=solver)
+        ok = st == 0
+        loss = (torch.where(ok, obj, torch.zeros_like(obj)) * g_obj).sum() + (x * g_x).sum()
+        torch.autograd.grad(loss, (A, b, c))
+
+    ms = _time(fwd_bwd, reps=3, warm=1)
+    out["mixed_20000_fwd_bwd"] = {"LPs_per_s": mix.count / (ms * 1e-3), "ms": ms}
+    del A, b, c, mix, sb
+    torch.cuda.empty_cache()
+    # hyperbox support functions, per-LP boxes and one shared box
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(3)
     for count, n, dt in ((4_000_000, 5, torch.float32), (6_000_000, 28, torch.float64)):
-        c = torch.randn((count, n), generator=g, device=dev, dtype=dt)
-        l = torch.rand((count, n), generator=g, device=dev, dtype=dt) * -10
-        u = torch.rand((count, n), generator=g, device=dev, dtype=dt) * 10
+        c = torch.randn((count, n), generator=gen, device=dev, dtype=dt)
+        l = -10 * torch.rand((count, n), generator=gen, device=dev, dtype=dt)
+        u = 10 * torch.rand((count, n), generator=gen, device=dev, dtype=dt)
         obj = torch.empty(count, dtype=dt, device=dev)
-        for _ in range(3):
-            solver.hyperbox(c, l, u, obj=obj)
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-        reps = 20
-        e0.record()
-        for _ in range(reps):
-            solver.hyperbox(c, l, u, obj=obj)
-        e1.record()
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / reps
         es = c.element_size()
-        gbs = (3 * n * es + es) * count / (ms * 1e-3) / 1e9
-        out[f"hyperbox_{count}x{n}_{'f32' if es == 4 else 'f64'}"] = {
-            "LPs_per_s": count / (ms * 1e-3), "ms": ms, "GB_per_s": gbs}
+        tag = "f32" if es == 4 else "f64"
+        ms = _time(lambda: solver.hyperbox(c, l, u, obj=obj), reps=20)
+        out[f"hyperbox_{count}x{n}_{tag}"] = {"LPs_per_s": count / (ms * 1e-3), "ms": ms,
+                                               "GB_per_s": (3 * n * es + es) * count / (ms * 1e-3) / 1e9}
+        ls, us = l[0].contiguous(), u[0].contiguous()
+        ms = _time(lambda: solver.hyperbox(c, ls, us, obj=obj), reps=20)
+        out[f"hyperbox_{count}x{n}_{tag}_shared_box"] = {"LPs_per_s": count / (ms * 1e-3), "ms": ms,
+                                                          "GB_per_s": (n * es + es) * count / (ms * 1e-3) / 1e9}
         del c, l, u, obj
+        torch.cuda.empty_cache()
     return out
 
 

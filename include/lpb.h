@@ -181,7 +181,8 @@ lpb_err lpb_sync_error(lpb_handle *handle, void *stream, uint32_t *word);
 typedef struct {
   int64_t resolved_fp64;
   int64_t deferred;
-  int64_t reserved[6];
+  int64_t kernels;        /* kernel launches of the last lpb_solve on this handle */
+  int64_t reserved[5];
 } lpb_stats;
 lpb_err lpb_get_stats(lpb_handle *handle, void *stream, lpb_stats *stats);
 

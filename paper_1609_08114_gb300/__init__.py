@@ -221,7 +221,7 @@ class Solver:
     def stats(self) -> dict:
         st = _lib.Stats()
         _lib.check(self.lib.lpb_get_stats(self.h, _stream_handle(self.device), ctypes.byref(st)), "lpb_get_stats")
-        return {"resolved_fp64": int(st.resolved_fp64), "deferred": int(st.deferred)}
+        return {"resolved_fp64": int(st.resolved_fp64), "deferred": int(st.deferred), "kernels": int(st.kernels)}
 
     def profile_start(self, calls: int):
         """Record per-pass kernel times (CUDA events on the solve's stream) for the next calls."""

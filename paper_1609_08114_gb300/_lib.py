@@ -44,8 +44,8 @@ class Options(ctypes.Structure):
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [("resolved_fp64", ctypes.c_int64), ("deferred", ctypes.c_int64),
-                ("reserved", ctypes.c_int64 * 6)]
+    _fields_ = [("resolved_fp64", ctypes.c_int64), ("deferred", ctypes.c_int64), ("kernels", ctypes.c_int64),
+                ("reserved", ctypes.c_int64 * 5)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/lpb.h

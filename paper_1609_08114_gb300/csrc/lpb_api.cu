@@ -24,6 +24,7 @@ struct lpb_handle {
   cudaEvent_t *prof_ev = nullptr;   // [kProfMax * 3 * 2]
   bool prof_ran[kProfMax * 3] = {};
   int prof_cap = 0, prof_n = 0;
+  int last_kernels = 0;             // kernel launches of the last lpb_solve
   // Autotuned schedules (lpb_autotune), by batch shape.
   struct Tuned {
     int max_m, max_n, dtype, prec;
@@ -301,7 +302,8 @@ lpb_err solve_workspace_bytes(const DeviceInfo &d, const lpb_batch *b, const lpb
 
 lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_batch *b,
                   const lpb_options *o, const lpb_result *r, void *ws, size_t ws_bytes, cudaStream_t s,
-                  cudaEvent_t *prof_ev, bool *prof_ran) {
+                  cudaEvent_t *prof_ev, bool *prof_ran, int *kernels) {
+  if (kernels) *kernels = 0;
   Plan pl;
   lpb_err e = make_plan(d, b, o, r->basis != nullptr, &pl);
   if (e != LPB_OK) return e;
@@ -333,6 +335,7 @@ lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_ba
         cp.lists = reinterpret_cast<int32_t *>(w + pl.off_lists);
         cp.class_count = class_count;
         if (launch_classify(cp, d.sms, s) != cudaSuccess) return LPB_ECUDA;
+        if (kernels) *kernels += 3;
       }
     }
     TableauParams p = base_params(ctr, err, b, r, o, pl, w);
@@ -362,6 +365,7 @@ lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_ba
     const cudaError_t ce = ps.reg >= 0 ? launch_reg(p, ps.reg, ps.grid, ps.smem, s)
                                        : launch_tableau(p, ps.fp64, ps.gmem, ps.grid, ps.threads, ps.smem, s);
     if (ce != cudaSuccess) return LPB_ECUDA;
+    if (kernels) *kernels += 1;
   }
   if (prof_ev && group >= 0 && cudaEventRecord(prof_ev[group * 2 + 1], s) != cudaSuccess) return LPB_ECUDA;
   return LPB_OK;
@@ -470,7 +474,7 @@ lpb_err lpb_solve(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const
   const lpb_err e = run_solve(device_info(h), h->d_ctr, h->d_err, b, o, r, ws, ws_bytes,
                               static_cast<cudaStream_t>(stream),
                               prof ? h->prof_ev + size_t(h->prof_n) * 3 * 2 : nullptr,
-                              prof ? h->prof_ran + h->prof_n * 3 : nullptr);
+                              prof ? h->prof_ran + h->prof_n * 3 : nullptr, &h->last_kernels);
   if (e == LPB_OK && prof) ++h->prof_n;
   return e;
 }
@@ -669,6 +673,7 @@ lpb_err lpb_get_stats(lpb_handle *h, void *stream, lpb_stats *st) {
   std::memset(st, 0, sizeof(*st));
   st->deferred = c[CTR_DEFER];
   st->resolved_fp64 = c[CTR_RESOLVE];
+  st->kernels = h->last_kernels;
   return LPB_OK;
 }
 

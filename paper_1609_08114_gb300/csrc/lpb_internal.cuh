@@ -258,6 +258,6 @@ lpb_err solve_workspace_bytes(const DeviceInfo &d, const lpb_batch *b, const lpb
 // with scratch from `ws`.  prof_ev (3 pairs) / prof_ran (3 flags) may be null.
 lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_batch *b,
                   const lpb_options *o, const lpb_result *r, void *ws, size_t ws_bytes, cudaStream_t s,
-                  cudaEvent_t *prof_ev, bool *prof_ran);
+                  cudaEvent_t *prof_ev, bool *prof_ran, int *kernels = nullptr);
 
 }  // namespace lpb

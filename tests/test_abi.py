@@ -60,7 +60,7 @@ def test_struct_layouts_match_header(tmp_path):
         "lpb_result": (_lib.Result, ["status", "iters", "obj", "x", "y", "basis"]),
         "lpb_options": (_lib.Options, ["prec", "max_iter", "eps_p", "eps_d", "feas_tol", "keep_basis_inverse",
                                        "kernel", "threads", "reg_warps"]),
-        "lpb_stats": (_lib.Stats, ["resolved_fp64", "deferred", "reserved"]),
+        "lpb_stats": (_lib.Stats, ["resolved_fp64", "deferred", "kernels", "reserved"]),
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lpb.h"', "int main(void){"]
     for cname, (_, fields) in checks.items():
