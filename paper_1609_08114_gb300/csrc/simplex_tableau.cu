@@ -84,6 +84,7 @@ struct Tab {
   unsigned char *ins;
   int m, n, k, nc, ld;   // nc = n + k non-RHS columns; column nc is the RHS
   int nm;                // variables >= nm are artificial
+  bool gmem;             // the tableau is a workspace slot (L2), not shared memory
 };
 
 // Step 3: pivot on (l, e), updating rows 0..rows-1.
@@ -100,13 +101,50 @@ __device__ void pivot(Tab<T> &S, int rows, int l, int e) {
     S.nonb[e] = v;
   }
   __syncthreads();
-  for (int i = wid; i < rows; i += nw) {
-    T *row = S.t + size_t(i) * ld;
-    if (i == l) {
-      for (int j = lane; j <= nc; j += 32) row[j] = (j == e) ? T(1) / p : S.rowb[j] / p;
-    } else {
-      const T f = S.colb[i];
-      for (int j = lane; j <= nc; j += 32) row[j] = (j == e) ? -f : fma(-f, S.rowb[j], row[j]);
+  if (!S.gmem) {           // shared-memory tableau: short latencies, plain loop
+    for (int i = wid; i < rows; i += nw) {
+      T *row = S.t + size_t(i) * ld;
+      if (i == l) {
+        for (int j = lane; j <= nc; j += 32) row[j] = (j == e) ? T(1) / p : S.rowb[j] / p;
+      } else {
+        const T f = S.colb[i];
+        for (int j = lane; j <= nc; j += 32) row[j] = (j == e) ? -f : fma(-f, S.rowb[j], row[j]);
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  // Slot tableau in L2: warps own rows, lanes own columns, and each lane loads
+  // kU elements of kR rows before it updates them, so a batch costs one round
+  // trip instead of one per element.
+  constexpr int kR = 2, kU = 4;
+  for (int i0 = wid; i0 < rows; i0 += nw * kR) {
+    for (int j0 = lane; j0 <= nc; j0 += 32 * kU) {
+      T v[kR][kU], rb[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int j = j0 + 32 * u;
+        rb[u] = j <= nc ? S.rowb[j] : T(0);
+#pragma unroll
+        for (int q = 0; q < kR; ++q) {
+          const int i = i0 + q * nw;
+          v[q][u] = (i < rows && j <= nc) ? S.t[size_t(i) * ld + j] : T(0);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kR; ++q) {
+        const int i = i0 + q * nw;
+        if (i >= rows) continue;
+        T *row = S.t + size_t(i) * ld;
+        const T f = S.colb[i];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int j = j0 + 32 * u;
+          if (j > nc) continue;
+          if (i == l) row[j] = (j == e) ? T(1) / p : rb[u] / p;
+          else row[j] = (j == e) ? -f : fma(-f, rb[u], v[q][u]);
+        }
+      }
     }
   }
   __syncthreads();
@@ -329,9 +367,44 @@ __device__ bool warm_start(Tab<T> &S, const int32_t *warm, int &iters, T eps_p) 
     ++iters;
   }
   int bad = 0;
-  for (int i = tid; i < m; i += nt)
-    bad |= (S.basic[i] >= nm) || !(S.t[size_t(i) * S.ld + S.nc] >= -eps_p);
+  for (int i = tid; i < m; i += nt) bad |= S.basic[i] >= nm;
   return !__syncthreads_or(bad);
+}
+
+// Dual simplex pivots from a basis that is (nearly) dual feasible but has
+// negative basic values: the most negative basic value leaves, the entering
+// column minimises r_j / -t_lj over t_lj < -eps_p.  Returns true once every
+// basic value is >= -eps_p; false if a row has no entering column or the cap
+// is reached (the caller then starts cold).
+template <typename T>
+__device__ bool dual_cleanup(Tab<T> &S, int rows, int &iters, int max_iter, T eps_p) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (;;) {
+    __syncthreads();
+    T v = pos_inf<T>();
+    int key = INT_MAX;
+    for (int i = tid; i < S.m; i += nt) {
+      const int bv = S.basic[i];
+      if (bv >= S.nm) continue;
+      const T rhs = S.t[size_t(i) * S.ld + S.nc];
+      if (rhs < -eps_p) keep_better(v, key, rhs, (bv << kIdxBits) | i);
+    }
+    block_argmin(v, key, S.redv, S.redk);
+    if (key == INT_MAX) return true;
+    const int l = key & kIdxMask;
+    v = pos_inf<T>();
+    key = INT_MAX;
+    for (int j = tid; j < S.nc; j += nt) {
+      const int var = S.nonb[j];
+      if (var >= S.nm) continue;
+      const T a = S.t[size_t(l) * S.ld + j];
+      if (a < -eps_p) keep_better(v, key, S.t[size_t(S.m) * S.ld + j] / -a, (var << kIdxBits) | j);
+    }
+    block_argmin(v, key, S.redv + 32, S.redk + 32);
+    if (key == INT_MAX || iters >= max_iter) return false;
+    pivot(S, rows, l, key & kIdxMask);
+    ++iters;
+  }
 }
 
 // Write the FP64 outputs of LP `lp` from the tableau (FP64 and plain FP32 modes).
@@ -516,6 +589,7 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
   S.redv = reinterpret_cast<T *>(smem + L.redv);
   S.redk = reinterpret_cast<int *>(smem + L.redk);
   S.ins = smem + L.ins;
+  S.gmem = kGmem;
   __shared__ int s_item, s_k;
   __shared__ unsigned long long s_bmax, s_cmax;
   const T eps_p = T(P.eps_p), eps_d = T(P.eps_d);
@@ -573,7 +647,8 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
     } else {
       bool warm = false;
       if (P.warm && basis_at(P, lp, boff)) {
-        warm = warm_start(S, basis_at(P, lp, boff), iters, eps_p);
+        warm = warm_start(S, basis_at(P, lp, boff), iters, eps_p) &&
+               dual_cleanup(S, m + (S.k ? 2 : 1), iters, max_iter, eps_p);
         if (!warm) {         // cold restart
           iters = 0;
           build_tableau(S, P.B, lp, aoff, boff, coff);
@@ -581,10 +656,17 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
       }
       status = LPB_OPTIMAL;
       if (S.k && !warm) {    // Phase I
+        // An FP32 tableau carries the Phase-I objective's round-off relative to
+        // its starting value (minus the sum of the negated right-hand sides), so
+        // its infeasibility test is relative to that; the FP64 certificate and
+        // re-solve settle the LPs it lets through.
+        const double w0 = -double(S.t[size_t(m + 1) * S.ld + S.nc]);
+        const double ftol = sizeof(T) == 4 ? fmax(P.feas_tol * (1.0 + bmax), 1e-5 * (1.0 + w0))
+                                           : P.feas_tol * (1.0 + bmax);
         status = run_phase(S, m + 1, m + 2, 1, iters, max_iter, eps_p, eps_d);
         if (status == LPB_OPTIMAL) {
           const double w = double(S.t[size_t(m + 1) * S.ld + S.nc]);
-          if (-w > P.feas_tol * (1.0 + bmax)) {
+          if (-w > ftol) {
             status = LPB_INFEASIBLE;
           } else {             // drive zero-level artificials out of the basis
             for (int i = 0; i < m; ++i) {
