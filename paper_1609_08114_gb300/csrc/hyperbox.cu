@@ -8,6 +8,10 @@
 // coalesced 16-byte loads, then each lane sums its own row from shared memory
 // in index order from +0.0, rounding every product and every sum separately
 // (no FMA contraction) so the result is reproducible bit for bit.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "lpb_internal.cuh"
 
 namespace lpb {
@@ -20,6 +24,15 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+// c < 0 (false for -0.0 and NaN).  For doubles the test runs on the integer
+// bits: the FP64 unit of this GPU is the bottleneck of the FP64 sum already.
+__device__ __forceinline__ bool negative(float c) { return c < 0.f; }
+__device__ __forceinline__ bool negative(double c) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(c));
+  const unsigned long long mag = u & 0x7fffffffffffffffull;
+  return (u >> 63) && mag != 0ull && mag <= 0x7ff0000000000000ull;
+}
 
 // Warp-cooperative copy of `len` elements; 16-byte vectors when both ends are
 // 16-byte aligned, scalar elements for the rest.
@@ -96,7 +109,7 @@ __global__ void __launch_bounds__(kWarps * 32) hyperbox_kernel(HyperboxParams P)
         if (lane < cnt) {
           for (int i = 0; i < ch; ++i) {
             const T ci = wc[lane * rs + i];
-            const T h = (ci < T(0)) ? (kShared ? sbox[i0 + i] : wl[lane * rs + i])
+            const T h = negative(ci) ? (kShared ? sbox[i0 + i] : wl[lane * rs + i])
                                     : (kShared ? sbox[n + i0 + i] : wu[lane * rs + i]);
             acc = add_rn(acc, mul_rn(ci, h));
             wc[lane * rs + i] = h;
@@ -129,7 +142,7 @@ __global__ void __launch_bounds__(kWarps * 32) hyperbox_kernel(HyperboxParams P)
       const T *row_u = kShared ? sbox + n : wu + size_t(lane) * n;
       for (int i = 0; i < n; ++i) {
         const T ci = row_c[i];
-        const T h = (ci < T(0)) ? row_l[i] : row_u[i];
+        const T h = negative(ci) ? row_l[i] : row_u[i];
         acc = add_rn(acc, mul_rn(ci, h));
         if (P.x) row_c[i] = h;          // the maximiser replaces c in place
       }
@@ -139,6 +152,152 @@ __global__ void __launch_bounds__(kWarps * 32) hyperbox_kernel(HyperboxParams P)
     if (P.x) {
       warp_copy_out(static_cast<T *>(P.x) + lp0 * n, wc, len, lane);
       __syncwarp();
+    }
+  }
+}
+
+// ---- TMA-streamed variant ------------------------------------------------
+//
+// CTA of `lps` threads, one LP per thread per chunk; chunk k of the CTA covers
+// LPs (blockIdx.x + k * gridDim.x) * lps ...  Thread 0 issues one bulk copy per
+// array per chunk into stage k % kStages and arms the stage's mbarrier with the
+// byte count; everyone waits on the barrier (bounded), sums its row from shared
+// memory, and the stage is refilled once all threads are past it.
+
+constexpr unsigned kWaitLimit = 1u << 26;   // try_wait rounds before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
+  unsigned ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(ok) : "r"(smem_u32(bar)), "r"(phase) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+
+template <typename T, bool kShared, int kStages>
+__global__ void hyperbox_tma_kernel(HyperboxParams P, int lps, uint32_t *err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[kStages];
+  const int tid = threadIdx.x, n = P.n;
+  const size_t row_bytes = size_t(n) * sizeof(T);
+  const size_t arr_bytes = size_t(lps) * row_bytes;          // one array of one chunk (multiple of 16)
+  const int narr = kShared ? 1 : 3;
+  const size_t box_bytes = kShared ? ((2 * row_bytes + 127) & ~size_t(127)) : 0;
+  T *sbox = reinterpret_cast<T *>(smem);
+  unsigned char *stage0 = smem + box_bytes;
+  const size_t stage_bytes = (narr * arr_bytes + 127) & ~size_t(127);
+  const int64_t nfull = P.count / lps;                      // chunks loaded by TMA
+  const T *gc = static_cast<const T *>(P.c), *gl = static_cast<const T *>(P.l), *gu = static_cast<const T *>(P.u);
+  if (kShared)
+    for (int i = tid; i < n; i += blockDim.x) { sbox[i] = gl[i]; sbox[n + i] = gu[i]; }
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  auto issue = [&](int64_t chunk, int s) {                   // thread 0 only
+    unsigned char *dst = stage0 + size_t(s) * stage_bytes;
+    const int64_t lp0 = chunk * lps;
+    mbar_expect_tx(&bars[s], unsigned(narr * arr_bytes));
+    bulk_load(dst, gc + lp0 * n, unsigned(arr_bytes), &bars[s]);
+    if (!kShared) {
+      bulk_load(dst + arr_bytes, gl + lp0 * n, unsigned(arr_bytes), &bars[s]);
+      bulk_load(dst + 2 * arr_bytes, gu + lp0 * n, unsigned(arr_bytes), &bars[s]);
+    }
+  };
+  // chunks of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int64_t mine = nfull > blockIdx.x ? (nfull - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  if (tid == 0)
+    for (int s = 0; s < kStages && s < mine; ++s) issue(blockIdx.x + int64_t(s) * gridDim.x, s);
+  bool failed = false;
+  for (int64_t k = 0; k < mine; ++k) {
+    const int s = int(k % kStages);
+    const unsigned phase = unsigned((k / kStages) & 1);
+    const int64_t chunk = blockIdx.x + k * gridDim.x;
+    unsigned tries = 0;
+    while (!mbar_try_wait(&bars[s], phase)) {
+      if (++tries >= kWaitLimit) { failed = true; break; }
+    }
+    if (__syncthreads_or(failed)) {
+      if (tid == 0) {
+        atomicOr(err, ERR_WAIT_TIMEOUT);
+        // Let the copies this CTA issued land before it exits (bounded again):
+        // stage s2 still expects the completion of chunk k2 = k, k+1, ... < mine.
+        for (int64_t k2 = k; k2 < k + kStages && k2 < mine; ++k2) {
+          unsigned t2 = 0;
+          while (!mbar_try_wait(&bars[k2 % kStages], unsigned((k2 / kStages) & 1)) && ++t2 < kWaitLimit) {
+          }
+        }
+      }
+      __syncthreads();
+      break;
+    }
+    T *wc = reinterpret_cast<T *>(stage0 + size_t(s) * stage_bytes);
+    const T *wl = reinterpret_cast<const T *>(reinterpret_cast<unsigned char *>(wc) + arr_bytes);
+    const T *wu = reinterpret_cast<const T *>(reinterpret_cast<unsigned char *>(wc) + 2 * arr_bytes);
+    const int64_t lp = chunk * lps + tid;
+    {
+      T acc = T(0);
+      T *rc = wc + size_t(tid) * n;
+      const T *rl = kShared ? sbox : wl + size_t(tid) * n;
+      const T *ru = kShared ? sbox + n : wu + size_t(tid) * n;
+      for (int i = 0; i < n; ++i) {
+        const T ci = rc[i];
+        const T h = negative(ci) ? rl[i] : ru[i];
+        acc = add_rn(acc, mul_rn(ci, h));
+        if (P.x) rc[i] = h;
+      }
+      static_cast<T *>(P.obj)[lp] = acc;
+    }
+    __syncthreads();                                          // stage s fully read
+    if (tid == 0) {
+      if (P.x) {                                              // the maximisers go back by bulk store
+        fence_async_smem();
+        bulk_store(static_cast<T *>(P.x) + chunk * lps * n, wc, unsigned(arr_bytes));
+        bulk_commit();
+        bulk_wait_read();
+      }
+      if (k + kStages < mine) {
+        fence_async_smem();
+        issue(blockIdx.x + (k + kStages) * gridDim.x, s);
+      }
+    }
+  }
+  if (tid == 0 && P.x) bulk_wait_read();
+  // The partial last chunk (count % lps LPs) with plain loads, by the last CTA.
+  const int64_t tail0 = nfull * lps;
+  if (blockIdx.x == gridDim.x - 1 && tail0 < P.count) {
+    const int64_t lp = tail0 + tid;
+    if (lp < P.count) {
+      T acc = T(0);
+      for (int i = 0; i < n; ++i) {
+        const T ci = gc[lp * n + i];
+        const T h = negative(ci) ? (kShared ? sbox[i] : gl[lp * n + i]) : (kShared ? sbox[n + i] : gu[lp * n + i]);
+        acc = add_rn(acc, mul_rn(ci, h));
+        if (P.x) static_cast<T *>(P.x)[lp * n + i] = h;
+      }
+      static_cast<T *>(P.obj)[lp] = acc;
     }
   }
 }
@@ -175,8 +334,88 @@ cudaError_t launch_t(const HyperboxParams &p, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch_hyperbox(const HyperboxParams &p, cudaStream_t s) {
+namespace {
+
+// Shared memory of the TMA variant with `lps` LPs per chunk and `stages` stages.
+size_t tma_smem(int n, int es, bool shared, int lps, int stages) {
+  const size_t row = size_t(n) * es;
+  const size_t box = shared ? ((2 * row + 127) & ~size_t(127)) : 0;
+  const size_t stage = ((shared ? 1 : 3) * size_t(lps) * row + 127) & ~size_t(127);
+  return box + size_t(stages) * stage;
+}
+
+constexpr size_t kTmaSmemMax = size_t(200) * 1024;
+
+// Resident CTAs per SM of `fn` at `smem` bytes, cached per (device, kernel,
+// CTA size, shared memory): the lookup runs once per shape, not per call.
+int cached_occupancy(const void *fn, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void *, int, size_t>, int> table;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const auto key = std::make_tuple(dev, fn, threads, smem);
+  std::lock_guard<std::mutex> lock(mu);
+  const auto it = table.find(key);
+  if (it != table.end()) return it->second;
+  int per_sm = 0;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTmaSmemMax)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess)
+    per_sm = 0;
+  table.emplace(key, per_sm);
+  return per_sm;
+}
+
+template <typename T, bool S>
+cudaError_t launch_tma(const HyperboxParams &p, uint32_t *err, cudaStream_t s, bool *launched) {
+  *launched = false;
+  const void *fns[2] = {reinterpret_cast<const void *>(hyperbox_tma_kernel<T, S, 1>),
+                        reinterpret_cast<const void *>(hyperbox_tma_kernel<T, S, 2>)};
+  // The row staging needs `stages * (1 or 3) * n` elements of shared memory per
+  // thread; the shape with the most resident threads per SM wins (double
+  // buffering, then longer chunks, on a tie).
+  int best_threads = 0, best_stages = 0, best_lps = 0, best_per_sm = 0;
+  for (int stages = 2; stages >= 1; --stages)
+    for (int lps = 128; lps >= 32; lps /= 2) {
+      const size_t smem = tma_smem(p.n, int(sizeof(T)), S, lps, stages);
+      if (smem > kTmaSmemMax) continue;
+      const int per_sm = cached_occupancy(fns[stages - 1], lps, smem);
+      if (per_sm * lps > best_threads) {
+        best_threads = per_sm * lps; best_stages = stages; best_lps = lps; best_per_sm = per_sm;
+      }
+    }
+  if (best_threads == 0) return cudaSuccess;               // caller falls back
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = tma_smem(p.n, int(sizeof(T)), S, best_lps, best_stages);
+  const int64_t nfull = p.count / best_lps;
+  int64_t grid = int64_t(sms) * best_per_sm;
+  if (grid > nfull) grid = nfull;
+  if (grid < 1) grid = 1;
+  if (best_stages == 2) hyperbox_tma_kernel<T, S, 2><<<int(grid), best_lps, smem, s>>>(p, best_lps, err);
+  else hyperbox_tma_kernel<T, S, 1><<<int(grid), best_lps, smem, s>>>(p, best_lps, err);
+  *launched = true;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_hyperbox(const HyperboxParams &p, uint32_t *err, cudaStream_t s) {
   if (p.count == 0) return cudaSuccess;
+  // Bulk copies need 16-byte aligned addresses; chunks of 32k rows are whole
+  // multiples of 16 bytes.
+  const uintptr_t al = reinterpret_cast<uintptr_t>(p.c) | reinterpret_cast<uintptr_t>(p.obj) |
+                       (p.shared_box ? 0 : reinterpret_cast<uintptr_t>(p.l) | reinterpret_cast<uintptr_t>(p.u)) |
+                       reinterpret_cast<uintptr_t>(p.x);
+  if ((al & 15) == 0) {
+    bool launched = false;
+    cudaError_t e;
+    if (p.dtype == LPB_DTYPE_F64)
+      e = p.shared_box ? launch_tma<double, true>(p, err, s, &launched) : launch_tma<double, false>(p, err, s, &launched);
+    else
+      e = p.shared_box ? launch_tma<float, true>(p, err, s, &launched) : launch_tma<float, false>(p, err, s, &launched);
+    if (launched || e != cudaSuccess) return e;
+  }
   if (p.dtype == LPB_DTYPE_F64)
     return p.shared_box ? launch_t<double, true>(p, s) : launch_t<double, false>(p, s);
   return p.shared_box ? launch_t<float, true>(p, s) : launch_t<float, false>(p, s);

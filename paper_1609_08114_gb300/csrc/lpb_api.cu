@@ -647,7 +647,7 @@ lpb_err lpb_hyperbox(lpb_handle *h, int64_t count, int32_t n, int32_t dtype, con
   const size_t smem = hyperbox_smem_bytes(n, dtype == LPB_DTYPE_F64 ? 8 : 4, shared_box != 0);
   if (smem > h->smem_optin) return LPB_EUNSUPPORTED;
   HyperboxParams p{count, n, dtype, shared_box != 0, c, l, u, obj, x};
-  return launch_hyperbox(p, static_cast<cudaStream_t>(stream)) == cudaSuccess ? LPB_OK : LPB_ECUDA;
+  return launch_hyperbox(p, h->d_err, static_cast<cudaStream_t>(stream)) == cudaSuccess ? LPB_OK : LPB_ECUDA;
 }
 
 lpb_err lpb_sync_error(lpb_handle *h, void *stream, uint32_t *word) {

@@ -23,6 +23,7 @@ enum : uint32_t {
   ERR_LIST_OVERFLOW = 1u,   // a work list received more entries than it can hold
   ERR_SLOT_OVERFLOW = 2u,   // an LP did not fit the tableau slot of its launch
   ERR_BAD_LAUNCH = 4u,      // a kernel was launched with an inconsistent configuration
+  ERR_WAIT_TIMEOUT = 8u,    // a bounded wait on an asynchronous copy gave up
 };
 
 enum Mode : int { MODE_FP64 = 0, MODE_FP32_REFINE = 1, MODE_FP32 = 2 };
@@ -235,7 +236,7 @@ void reg_limits(int cfg, int *max_m, int *max_n, int *warps);
 cudaError_t reg_occupancy(int cfg, int max_m, int max_n, int dtype, int *ctas, int *threads, size_t *smem);
 cudaError_t launch_reg(const TableauParams &p, int cfg, int grid, size_t smem, cudaStream_t s);
 size_t hyperbox_smem_bytes(int n, int elem_bytes, bool shared_box);
-cudaError_t launch_hyperbox(const HyperboxParams &p, cudaStream_t s);
+cudaError_t launch_hyperbox(const HyperboxParams &p, uint32_t *err, cudaStream_t s);
 // Backward kernel (backward.cu).
 size_t backward_smem_bytes(int max_m, int max_n);
 size_t backward_slot_bytes(int max_m, int max_n);
