@@ -164,48 +164,17 @@ __global__ void __launch_bounds__(kWarps * 32) hyperbox_kernel(HyperboxParams P)
 // byte count; everyone waits on the barrier (bounded), sums its row from shared
 // memory, and the stage is refilled once all threads are past it.
 
-constexpr unsigned kWaitLimit = 1u << 26;   // try_wait rounds before giving up
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
-               "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
-  unsigned ok;
-  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-               : "=r"(ok) : "r"(smem_u32(bar)), "r"(phase) : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
-               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_u32(src)),
-               "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
-
 template <typename T, bool kShared, int kStages>
 __global__ void hyperbox_tma_kernel(HyperboxParams P, int lps, uint32_t *err) {
-  extern __shared__ __align__(128) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char hb_smem[];
   __shared__ __align__(8) uint64_t bars[kStages];
   const int tid = threadIdx.x, n = P.n;
   const size_t row_bytes = size_t(n) * sizeof(T);
   const size_t arr_bytes = size_t(lps) * row_bytes;          // one array of one chunk (multiple of 16)
   const int narr = kShared ? 1 : 3;
   const size_t box_bytes = kShared ? ((2 * row_bytes + 127) & ~size_t(127)) : 0;
-  T *sbox = reinterpret_cast<T *>(smem);
-  unsigned char *stage0 = smem + box_bytes;
+  T *sbox = reinterpret_cast<T *>(hb_smem);
+  unsigned char *stage0 = hb_smem + box_bytes;
   const size_t stage_bytes = (narr * arr_bytes + 127) & ~size_t(127);
   const int64_t nfull = P.count / lps;                      // chunks loaded by TMA
   const T *gc = static_cast<const T *>(P.c), *gl = static_cast<const T *>(P.l), *gu = static_cast<const T *>(P.u);

@@ -74,33 +74,141 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 constexpr int kBad = 1 << 30;   // a key larger than any real key
 
+// Bulk prefetch of [p, p + bytes) into L2, shrunk to whole 16-byte units
+// inside the range; a hint with no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
+  const uintptr_t lo = (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15);
+  const uintptr_t hi = (reinterpret_cast<uintptr_t>(p) + bytes) & ~uintptr_t(15);
+  if (hi > lo && hi - lo < (uintptr_t(1) << 31))
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(lo), "r"(unsigned(hi - lo)) : "memory");
+}
+
+// Prefetch A, b and c of work item `item` into L2 when the LP fits the launch.
+__device__ __forceinline__ void prefetch_lp(const TableauParams &P, int item) {
+  const int lp = P.in.items ? P.in.items[item] : item;
+  const int m = P.B.m[lp], n = P.B.n[lp];
+  if (m < 1 || n < 1 || m > P.lim_m || n > P.lim_n || m > P.B.max_m || n > P.B.max_n) return;
+  const size_t es = P.B.dtype == LPB_DTYPE_F64 ? 8 : 4;
+  prefetch_l2(static_cast<const unsigned char *>(P.B.A) + size_t(P.B.a_off[lp]) * es, size_t(m) * size_t(n) * es);
+  prefetch_l2(static_cast<const unsigned char *>(P.B.b) + size_t(P.B.b_off[lp]) * es, size_t(m) * es);
+  prefetch_l2(static_cast<const unsigned char *>(P.B.c) + size_t(P.B.c_off[lp]) * es, size_t(n) * es);
+}
+
+// Step 1-2 result of one warp for one pivot: its best entering column and
+// that column's min-ratio row.
+struct WarpChoice {
+  float v;       // reduced cost (0 under Bland's rule), +inf if none
+  int key;       // (entering variable << kIdxBits) | column, kBad if none
+  float theta;   // min ratio
+  int lkey;      // (leaving variable << kIdxBits) | row, kBad if unbounded
+};
+
+// Element i of an input vector staged in shared memory with its input dtype.
+__device__ __forceinline__ double vin(const double *v, int i, int dt) {
+  return dt == LPB_DTYPE_F64 ? v[i] : double(reinterpret_cast<const float *>(v)[i]);
+}
+
 template <int R, int C, int W>
 struct RegShared {
   static constexpr int ROWS = 32 * R, COLS = W * C;
-  float colbuf[ROWS];
+  float colbuf[2][W][ROWS];                  // each warp's candidate column, by pivot parity
+  WarpChoice choice[2][W];                   // by pivot parity
+  double bin[ROWS], cin[COLS];               // the LP's b and c as given (FP64 or FP32)
   float rhs[ROWS];
   int basic[ROWS];
   int nonb[COLS];
-  float candv[W];
-  int candk[W];
   alignas(16) float objv[W][(C + 3) & ~3];   // objective row, per warp
-  int l, leave_var, status, item;
-  float theta;
-  int nsb, nns;
+  int item, nsb, nns;
   unsigned long long bmax, cmax;
-  double xb[ROWS], rr[ROWS], yv[ROWS], rho[ROWS];
+  uint64_t abar;                             // completion of the bulk copies of A
+  double xb[ROWS], rr[ROWS], yv[ROWS], sax[ROWS], dj[COLS];
   float part[W][ROWS];
-  float rhof[ROWS];
-  int sb[ROWS], ns[COLS], sp[ROWS];
+  float rhof[ROWS], rrf[ROWS], dxf[ROWS], dyf[ROWS];
+  int posx[COLS];
+  int sb[ROWS], jb[ROWS], sp[ROWS];
+  int ns[COLS], kr[COLS];
   double red[2][W];
 };
 
 template <int R, int C, int W>
 __host__ __device__ constexpr size_t reg_fixed_bytes() { return (sizeof(RegShared<R, C, W>) + 15) & ~size_t(15); }
 
-// Row stride (in elements) of the resident copy of A: odd, so lanes reading
-// consecutive rows of one column hit distinct banks.
-__host__ __device__ inline int a_stride(int max_n) { return max_n | 1; }
+// Row stride (in elements) of the resident copy of A.  Rows start on 16-byte
+// boundaries (bulk copies), and the stride in 16-byte units is odd, so the
+// lanes of a warp reading one column touch as few banks twice as that allows.
+__host__ __device__ inline int a_stride(int max_n, int es) {
+  const int per = 16 / es;                                // elements per 16 bytes
+  int s = (max_n + per - 1) / per;
+  if ((s & 1) == 0) ++s;
+  return s * per;
+}
+
+// FP64 -> FP32 round to nearest even on the integer bits, without branches.
+// Magnitudes below the smallest normal float become a signed zero; magnitudes
+// that round beyond the float range, infinities and NaNs set `bad`.
+__device__ __forceinline__ float d2f_tile(double d, int &bad) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(d));
+  const unsigned hi = unsigned(u >> 32), lo = unsigned(u);
+  const unsigned ahi = hi & 0x7fffffffu;
+  unsigned f = ((ahi - (896u << 20)) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  f += unsigned(rem > 0x10000000u) | (unsigned(rem == 0x10000000u) & f);
+  const bool normal = ahi >= (897u << 20);
+  bad |= int(ahi >= (1151u << 20)) | int(normal & (f >= 0x7f800000u));
+  return __uint_as_float((hi & 0x80000000u) | (normal ? f : 0u));
+}
+
+// Smallest power of two >= k (1 <= k <= 32).
+__host__ __device__ constexpr int pow2_at_least(int k) { return k <= 1 ? 1 : 2 * pow2_at_least((k + 1) / 2); }
+
+// Sums v[c] over the 32 lanes of a warp for every c < P (P a power of two):
+// log2(P) halving exchanges, in which each lane keeps half of its columns and
+// adds the partner's copy of them, then plain butterflies.  On return lane l
+// holds the total of column l / (32 / P): P - 1 + log2(32 / P) shuffles in
+// place of 5 P.
+template <int P>
+__device__ __forceinline__ float reduce_scatter(float (&v)[P], int lane) {
+#pragma unroll
+  for (int h = P / 2, off = 16; h >= 1; h /= 2, off /= 2) {
+    const bool upper = (lane & off) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const float send = upper ? v[k] : v[k + h];
+      const float keep = upper ? v[k + h] : v[k];
+      v[k] = keep + __shfl_xor_sync(kFull, send, off);
+    }
+  }
+  float s = v[0];
+#pragma unroll
+  for (int off = 16 / P; off >= 1; off /= 2) s += __shfl_xor_sync(kFull, s, off);
+  return s;
+}
+
+// Input element i of a staged vector rounded to FP32 without branches (see
+// d2f_tile); non-finite or out-of-range values set `bad`.
+__device__ __forceinline__ float vin_tile(const double *v, int i, int dt, int &bad) {
+  if (dt == LPB_DTYPE_F64) return d2f_tile(v[i], bad);
+  const float f = reinterpret_cast<const float *>(v)[i];
+  bad |= !isfinite(f);
+  return f;
+}
+
+// A double's high word as a float, truncated to 20 mantissa bits (relative
+// error below 2^-20), in integer operations: magnitudes below the float range
+// give 0, above it infinity.  Used where FP32 accuracy is ample (products with
+// the small refinement corrections).
+__device__ __forceinline__ float hi2f(unsigned hi) {
+  const unsigned ahi = hi & 0x7fffffffu;
+  const unsigned f = ahi < (897u << 20) ? 0u : (ahi >= (1151u << 20) ? 0x7f800000u : ((ahi - (896u << 20)) << 3));
+  return __uint_as_float((hi & 0x80000000u) | f);
+}
+
+// Approximate reciprocal (one special-function-unit instruction, about 1 ulp).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
 
 template <typename T>
 __device__ __forceinline__ double a_at(const unsigned char *sa, int dt, int idx) {
@@ -108,8 +216,13 @@ __device__ __forceinline__ double a_at(const unsigned char *sa, int dt, int idx)
                              : double(reinterpret_cast<const float *>(sa)[idx]);
 }
 
+// Minimum resident CTAs per SM: more for the small tableaux, fewer for the
+// 4-warp CTAs with 128 rows, whose tableau alone takes C * 4 registers.
 template <int R, int C, int W>
-__global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauParams P) {
+constexpr int reg_min_blocks() { return R * C <= 8 ? (W <= 4 ? 4 : 3) : (R == 4 && W <= 4) ? 2 : (W <= 4 ? 3 : 2); }
+
+template <int R, int C, int W>
+__global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(TableauParams P) {
   using SH = RegShared<R, C, W>;
   constexpr int ROWS = SH::ROWS, COLS = SH::COLS;
   constexpr int NT = W * 32;
@@ -119,12 +232,23 @@ __global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauPa
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const float eps_p = float(P.eps_p), eps_d = float(P.eps_d);
   const int dt = P.B.dtype;
-  const int sld = a_stride(P.lim_n);
+  const int es = dt == LPB_DTYPE_F64 ? 8 : 4;
+  const int sld = a_stride(P.lim_n, es);
   const int nitems = P.in.count ? min(*P.in.count, P.list_cap) : P.B.count;
   float T[R][C];
 
+  if (tid == 0) {
+    mbar_init(&sh.abar, 1);
+    fence_mbar_init();
+  }
+  unsigned aphase = 0;        // parity of the next completion of sh.abar
+  // Lane 0 of the last warp claims work items one LP ahead, so that the next
+  // LP's data can be prefetched into L2 while this one is solved.
+  const int claimer = NT - 32;
+  int next = 0;
+  if (tid == claimer) next = atomicAdd(P.queue, 1);
   for (;;) {
-    if (tid == 0) sh.item = atomicAdd(P.queue, 1);
+    if (tid == claimer) sh.item = next;
     __syncthreads();
     const int item = sh.item;
     if (item >= nitems) break;
@@ -134,38 +258,92 @@ __global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauPa
     // ---- admission: sizes that fit the template, b >= 0, finite b and c ----
     const bool fits = m >= 1 && n >= 1 && m <= ROWS - 1 && n <= COLS - 1 && m <= P.B.max_m && n <= P.B.max_n &&
                       m <= P.lim_m && n <= P.lim_n;
-    if (fits) {    // start streaming A now; its copies land while b and c are checked
+    const unsigned char *Ag = static_cast<const unsigned char *>(P.B.A) + aoff * es;
+    // Rows of A whose global start and length are whole 16-byte units go by
+    // bulk copy (the copy engine, one instruction per row); others by 4- or
+    // 8-byte asynchronous copies.
+    const bool bulk = fits && ((reinterpret_cast<uintptr_t>(Ag) | uintptr_t(n) * es) & 15) == 0;
+    if (fits) {    // b and c first, then A; A's copies land while b and c are checked
       if (dt == LPB_DTYPE_F64) {
-        const double *A = static_cast<const double *>(P.B.A) + aoff;
-        double *s = reinterpret_cast<double *>(sA);
-        for (int i = wid; i < m; i += W)
-          for (int j = lane; j < n; j += 32) cp_async8(s + i * sld + j, A + int64_t(i) * n + j);
+        const double *bg = static_cast<const double *>(P.B.b) + boff, *cg = static_cast<const double *>(P.B.c) + coff;
+        for (int i = tid; i < m; i += NT) cp_async8(sh.bin + i, bg + i);
+        for (int j = tid; j < n; j += NT) cp_async8(sh.cin + j, cg + j);
       } else {
-        const float *A = static_cast<const float *>(P.B.A) + aoff;
-        float *s = reinterpret_cast<float *>(sA);
-        for (int i = wid; i < m; i += W)
-          for (int j = lane; j < n; j += 32) cp_async4(s + i * sld + j, A + int64_t(i) * n + j);
+        const float *bg = static_cast<const float *>(P.B.b) + boff, *cg = static_cast<const float *>(P.B.c) + coff;
+        for (int i = tid; i < m; i += NT) cp_async4(reinterpret_cast<float *>(sh.bin) + i, bg + i);
+        for (int j = tid; j < n; j += NT) cp_async4(reinterpret_cast<float *>(sh.cin) + j, cg + j);
       }
+      if (bulk) {
+        if (wid == 0) {
+          if (lane == 0) mbar_expect_tx(&sh.abar, unsigned(m) * unsigned(n) * unsigned(es));
+          __syncwarp();
+          for (int i = lane; i < m; i += 32)
+            bulk_load(sA + size_t(i) * sld * es, Ag + size_t(i) * n * es, unsigned(n) * es, &sh.abar);
+        }
+      } else if (dt == LPB_DTYPE_F64) {
+        const double *A = reinterpret_cast<const double *>(Ag);
+        double *sa = reinterpret_cast<double *>(sA);
+        for (int i = wid; i < m; i += W)
+          for (int j = lane; j < n; j += 32) cp_async8(sa + i * sld + j, A + int64_t(i) * n + j);
+      } else {
+        const float *A = reinterpret_cast<const float *>(Ag);
+        float *sa = reinterpret_cast<float *>(sA);
+        for (int i = wid; i < m; i += W)
+          for (int j = lane; j < n; j += 32) cp_async4(sa + i * sld + j, A + int64_t(i) * n + j);
+      }
+    }
+    if (tid == claimer) {
+      next = atomicAdd(P.queue, 1);
+      if (next < nitems) prefetch_lp(P, next);
     }
     int neg = 0;
     if (tid == 0) { sh.bmax = 0ull; sh.cmax = 0ull; }
+    cp_async_wait_all();
     __syncthreads();
     if (fits) {
-      double bm = 0.0, cm = 0.0;
+      // On the bits of the doubles (integer operations; FP64 ones have long
+      // latency here): |v| orders like its bit pattern.  b_i < 0 or NaN and
+      // non-finite c_j send the LP elsewhere.
+      constexpr unsigned long long kMag = 0x7fffffffffffffffull, kInf = 0x7ff0000000000000ull;
+      unsigned long long bm = 0ull, cm = 0ull;
       for (int i = tid; i < m; i += NT) {
-        const double v = ld_in(P.B.b, boff + i, dt);
-        neg |= !(v >= 0.0);   // negative or NaN
-        bm = fmax(bm, fabs(v));
+        const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(vin(sh.bin, i, dt)));
+        const unsigned long long a = u & kMag;
+        neg |= int((u >> 63) != 0ull && a != 0ull) | int(a > kInf);
+        bm = a > bm ? a : bm;
       }
       for (int j = tid; j < n; j += NT) {
-        const double v = ld_in(P.B.c, coff + j, dt);
-        neg |= !finite_bits(v);
-        cm = fmax(cm, fabs(v));
+        const unsigned long long a =
+            static_cast<unsigned long long>(__double_as_longlong(vin(sh.cin, j, dt))) & kMag;
+        neg |= int(a >= kInf);
+        cm = a > cm ? a : cm;
       }
-      if (bm == bm) atomicMax(&sh.bmax, static_cast<unsigned long long>(__double_as_longlong(bm)));
-      if (cm == cm) atomicMax(&sh.cmax, static_cast<unsigned long long>(__double_as_longlong(cm)));
+      if (bm > 0ull && bm <= kInf) atomicMax(&sh.bmax, bm);
+      if (cm > 0ull && cm < kInf) atomicMax(&sh.cmax, cm);
     }
-    cp_async_wait_all();
+    int timed_out = 0;
+    if (bulk) {
+      timed_out = !mbar_wait_bounded(&sh.abar, aphase);
+      aphase ^= 1u;
+    }
+    if (__syncthreads_or(timed_out)) {
+      // The copy engine did not deliver A in time: hand this LP and the one
+      // claimed after it to the generic kernel, give the copies one more
+      // bounded wait, and stop this CTA.
+      if (tid == 0) {
+        atomicOr(P.err, ERR_WAIT_TIMEOUT);
+        P.R.status[lp] = STATUS_PENDING;
+        list_push(P.defer_items, P.defer_count, P.list_cap, lp, P.err);
+        mbar_wait_bounded(&sh.abar, aphase ^ 1u);
+      }
+      if (tid == claimer && next < nitems) {
+        const int lp2 = P.in.items ? P.in.items[next] : next;
+        P.R.status[lp2] = STATUS_PENDING;
+        list_push(P.defer_items, P.defer_count, P.list_cap, lp2, P.err);
+      }
+      __syncthreads();
+      break;
+    }
     neg = __syncthreads_or(neg);
     if (!fits || neg) {      // the shared-memory kernel handles it (Phase I, sizes, bad data)
       if (tid == 0) {
@@ -180,24 +358,52 @@ __global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauPa
 
     // ---- the tableau: A rounded to FP32, b in column COLS-1, -c in row ROWS-1 ----
     int bad = 0;
+    if (dt == LPB_DTYPE_F64) {
+      const double *sa = reinterpret_cast<const double *>(sA);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = lane + 32 * r;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int j = wid + W * c;
+          T[r][c] = (i < m && j < n) ? d2f_tile(sa[i * sld + j], bad) : 0.f;
+        }
+      }
+    } else {
+      const float *sa = reinterpret_cast<const float *>(sA);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int i = lane + 32 * r;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int j = wid + W * c;
+          const float v = (i < m && j < n) ? sa[i * sld + j] : 0.f;
+          bad |= !isfinite(v);
+          T[r][c] = v;
+        }
+      }
+    }
+    // Every lane keeps, for its rows lane + 32 r, the basic variable and the
+    // right-hand side (the same FP32 values warp W-1 holds in its last
+    // column); lane c < C keeps the variable of the warp's column wid + W c.
+    int bvar[R];
+    float rhsr[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int i = lane + 32 * r;
+      rhsr[r] = i < m ? vin_tile(sh.bin, i, dt, bad) : 0.f;
+      bvar[r] = i < m ? n + i : kBad >> kIdxBits;
+    }
+    int nvar = (wid + W * lane < n && lane < C) ? wid + W * lane : kBad >> kIdxBits;
+    if (wid == W - 1) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) T[r][C - 1] = rhsr[r];
+    }
+    if (lane == 31) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         const int j = wid + W * c;
-        float v = 0.f;
-        if (i < m && j < n) {
-          if (dt == LPB_DTYPE_F64) {
-            const double a = reinterpret_cast<const double *>(sA)[i * sld + j];
-            bad |= !finite_bits(a);
-            v = d2f_rn(a);
-          } else {
-            v = reinterpret_cast<const float *>(sA)[i * sld + j];
-            bad |= !isfinite(v);
-          }
-        }
-        T[r][c] = v;
+        if (j < n) T[R - 1][c] = -vin_tile(sh.cin, j, dt, bad);
       }
     }
     bad = __syncthreads_or(bad);
@@ -209,34 +415,20 @@ __global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauPa
       __syncthreads();
       continue;
     }
-    if (wid == W - 1) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int i = lane + 32 * r;
-        const float v = i < m ? ld_as<float>(P.B.b, boff + i, dt) : 0.f;
-        T[r][C - 1] = v;
-        sh.rhs[i] = v;
-      }
-    }
-    if (lane == 31) {
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const int j = wid + W * c;
-        if (j < n) T[R - 1][c] = -ld_as<float>(P.B.c, coff + j, dt);
-      }
-    }
-    for (int i = tid; i < ROWS; i += NT) sh.basic[i] = i < m ? n + i : kBad >> kIdxBits;
-    for (int j = tid; j < COLS; j += NT) sh.nonb[j] = j < n ? j : kBad >> kIdxBits;
 
-    // ---- Steps 1-3 ----
+    // ---- Steps 1-3, one block barrier per pivot ----
+    // Each warp takes its own best entering column (Step 1 over its columns)
+    // and runs the min-ratio test on it (Step 2); after the barrier every warp
+    // picks the best of the W choices, and the pivot column comes from the
+    // winning warp's slot.  Slots are double-buffered by pivot parity: a warp
+    // can be at most one barrier ahead of the others.
     const int max_iter = P.max_iter > 0 ? P.max_iter : 50 * (m + n);
     int iters = 0, status = LPB_OPTIMAL, degenerate_run = 0;
     bool bland = false;
-    // Step 1 candidates: lane 31 publishes the warp's objective-row entries
-    // with 16-byte stores; lane c judges column wid + W c.  Column `ecol` (if
-    // >= 0) holds variable `evar`, whose nonb[] entry is rewritten meanwhile.
     float *objw = sh.objv[wid];
-    auto candidates = [&](int ecol, int evar) {
+    for (int par = 0;; par ^= 1) {
+      // Step 1 in this warp: lane 31 publishes the objective row with 16-byte
+      // stores; lane c judges column wid + W c.
       if (lane == 31) {
 #pragma unroll
         for (int c = 0; c < C; c += 4) {
@@ -249,100 +441,93 @@ __global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauPa
         }
       }
       __syncwarp();
-      float v = __int_as_float(0x7f800000);
-      int key = kBad;
-      const int j = wid + W * lane;
-      if (lane < C && j < COLS - 1) {                  // the last column is the right-hand side
-        const float rj = objw[lane];
-        if (rj < -eps_d) {
-          const int var = (j == ecol) ? evar : sh.nonb[j];
-          v = bland ? 0.f : rj;
-          key = (var << kIdxBits) | j;
+      float cv = __int_as_float(0x7f800000);
+      int ck = kBad;
+      {
+        const int j = wid + W * lane;
+        if (lane < C && j < COLS - 1) {                // the last column is the right-hand side
+          const float rj = objw[lane];
+          if (rj < -eps_d) {
+            cv = bland ? 0.f : rj;
+            ck = (nvar << kIdxBits) | j;
+          }
         }
       }
-      warp_argmin_f32(v, key);
-      if (lane == 0) {
-        sh.candv[wid] = v;
-        sh.candk[wid] = key;
-      }
-    };
-    __syncthreads();
-    candidates(-1, 0);
-    __syncthreads();
-    for (;;) {
-      float ev = lane < W ? sh.candv[lane] : __int_as_float(0x7f800000);
-      int ek = lane < W ? sh.candk[lane] : kBad;
-      warp_argmin_f32(ev, ek);
-      if (ek == kBad) { status = LPB_OPTIMAL; break; }
-      const int e = ek & kIdxMask;
-      const int we = e % W, ce = e / W;
-      float col[R];
-      if (wid == we) {
-        // Step 2 inside the warp that owns column e.
+      warp_argmin_f32(cv, ck);
+      // Step 2 on this warp's candidate.
+      float tv = __int_as_float(0x7f800000);
+      int tk = kBad;
+      if (ck != kBad) {
+        const int ce = (ck & kIdxMask) / W;
+        float col[R];
         dispatch<0, C>(ce, [&](auto K) {
 #pragma unroll
           for (int r = 0; r < R; ++r) col[r] = T[r][K.value];
         });
-        float v = __int_as_float(0x7f800000);
-        int key = kBad;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int i = lane + 32 * r;
-          if (col[r] > eps_p) keep_better(v, key, sh.rhs[i] * __frcp_rn(col[r]), (sh.basic[i] << kIdxBits) | i);
+          if (col[r] > eps_p) keep_better(tv, tk, rhsr[r] * rcp_approx(col[r]), (bvar[r] << kIdxBits) | i);
         }
-        warp_argmin_f32(v, key);
+        warp_argmin_f32(tv, tk);
 #pragma unroll
-        for (int r = 0; r < R; ++r) sh.colbuf[lane + 32 * r] = col[r];
-        if (lane == 0) {
-          if (key == kBad) {
-            sh.status = LPB_UNBOUNDED;
-          } else {
-            const int l = key & kIdxMask;
-            sh.status = LPB_OPTIMAL;
-            sh.l = l;
-            sh.theta = v;
-            sh.leave_var = sh.basic[l];
-          }
-        }
+        for (int r = 0; r < R; ++r) sh.colbuf[par][wid][lane + 32 * r] = col[r];
       }
-      __syncthreads();                                                      // B1
-      if (sh.status == LPB_UNBOUNDED) { status = LPB_UNBOUNDED; break; }
+      if (lane == 0) sh.choice[par][wid] = WarpChoice{cv, ck, tv, tk};
+      __syncthreads();
+      // The pivot: the best (value, key) over the warps' choices.
+      float ev = __int_as_float(0x7f800000);
+      int ek = kBad;
+      if (lane < W) {
+        ev = sh.choice[par][lane].v;
+        ek = sh.choice[par][lane].key;
+      }
+      warp_argmin_f32(ev, ek);
+      if (ek == kBad) { status = LPB_OPTIMAL; break; }
+      const int e = ek & kIdxMask;
+      const int we = e % W, ce = e / W;
+      const WarpChoice &wc = sh.choice[par][we];
+      const int lk = wc.lkey;
+      const float theta = wc.theta;
+      if (lk == kBad) { status = LPB_UNBOUNDED; break; }
       if (iters >= max_iter) { status = LPB_ITER_LIMIT; break; }
-      const int l = sh.l;
-      const float theta = sh.theta;
+      const int l = lk & kIdxMask, leave_var = lk >> kIdxBits;
       const int lr = l >> 5, ll = l & 31;
-      const float p = sh.colbuf[l];
-      const float rp = 1.f / p;
+      const float *pcol = sh.colbuf[par][we];
+      const float rp = __frcp_rn(pcol[l]);
       float cf[R];           // pivot column; 0 on the pivot row, which is only scaled
+      float gf[R];           // pivot column / p
 #pragma unroll
-      for (int r = 0; r < R; ++r) cf[r] = (lane + 32 * r == l) ? 0.f : sh.colbuf[lane + 32 * r];
-      // Step 3: the owner lane scales the pivot row by 1/p in place, then every
-      // warp takes its part of it by shuffles: T -= (pivot column) (x) (new pivot row).
+      for (int r = 0; r < R; ++r) {
+        cf[r] = (lane + 32 * r == l) ? 0.f : pcol[lane + 32 * r];
+        gf[r] = cf[r] * rp;
+      }
+      // Step 3: every lane takes the pivot row from lane ll by shuffles:
+      // T -= (pivot column / p) (x) (pivot row); the owner lane scales its
+      // row by 1/p.
       dispatch<0, R>(lr, [&](auto LR) {
-        if (lane == ll) {
-#pragma unroll
-          for (int c = 0; c < C; ++c) T[LR.value][c] *= rp;
-        }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           const float pr = __shfl_sync(kFull, T[LR.value][c], ll);
 #pragma unroll
-          for (int r = 0; r < R; ++r) T[r][c] = fmaf(-cf[r], pr, T[r][c]);
+          for (int r = 0; r < R; ++r) T[r][c] = fmaf(-gf[r], pr, T[r][c]);
+        }
+        const float prh = __shfl_sync(kFull, rhsr[LR.value], ll);
+#pragma unroll
+        for (int r = 0; r < R; ++r) rhsr[r] = fmaf(-gf[r], prh, rhsr[r]);
+        if (lane == ll) {
+#pragma unroll
+          for (int c = 0; c < C; ++c) T[LR.value][c] *= rp;
+          rhsr[LR.value] *= rp;
+          bvar[LR.value] = ek >> kIdxBits;
         }
       });
       if (wid == we) {        // new column e: -t_ie / p, and 1/p at the pivot
         dispatch<0, C>(ce, [&](auto K) {
 #pragma unroll
-          for (int r = 0; r < R; ++r) T[r][K.value] = (lane + 32 * r == l) ? rp : -col[r] * rp;
+          for (int r = 0; r < R; ++r) T[r][K.value] = (lane + 32 * r == l) ? rp : -cf[r] * rp;
         });
-      }
-      if (tid == 0) {
-        sh.basic[l] = ek >> kIdxBits;
-        sh.nonb[e] = sh.leave_var;
-      }
-      if (wid == W - 1) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) sh.rhs[lane + 32 * r] = T[r][C - 1];
+        if (lane == ce) nvar = leave_var;
       }
       ++iters;
       if (theta <= eps_p) {
@@ -351,9 +536,18 @@ __global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauPa
         degenerate_run = 0;
         bland = false;
       }
-      candidates(e, sh.leave_var);
-      __syncthreads();                                                      // B2
     }
+    // The final basis and right-hand side back to shared memory (every warp
+    // holds the same copy of the rows; warp 0 writes them).
+    if (wid == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        sh.basic[lane + 32 * r] = bvar[r];
+        sh.rhs[lane + 32 * r] = rhsr[r];
+      }
+    }
+    if (lane < C) sh.nonb[wid + W * lane] = nvar;
+    __syncthreads();
 
     int32_t *bp = P.bbuf ? P.bbuf + (P.bpacked ? boff : int64_t(lp) * P.B.max_m) : nullptr;
     if (status != LPB_OPTIMAL || P.mode != MODE_FP32_REFINE) {
@@ -397,22 +591,36 @@ __global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauPa
     }
 
     // ---- FP64 refinement and certificate, with A read from shared memory ----
-    if (wid == 0) {      // structural basic rows, non-basic slack columns (in order)
+    // Lists: the q-th basic structural sits in row sb[q] and column jb[q] of
+    // A; the p-th non-basic slack sits in tableau column ns[p] and row kr[p]
+    // of A.  Warp 0 builds the row lists, warp 1 the column lists.
+    if (wid == 0) {
       int base = 0;
       for (int i0 = 0; i0 < m; i0 += 32) {
         const int i = i0 + lane;
-        const bool pr = i < m && sh.basic[i] < n;
+        const int v = i < m ? sh.basic[i] : n;
+        const bool pr = i < m && v < n;
         const unsigned mk = __ballot_sync(kFull, pr);
-        if (pr) sh.sb[base + __popc(mk & ((1u << lane) - 1u))] = i;
+        if (pr) {
+          const int q = base + __popc(mk & ((1u << lane) - 1u));
+          sh.sb[q] = i;
+          sh.jb[q] = v;
+        }
         base += __popc(mk);
       }
       if (lane == 0) sh.nsb = base;
-      base = 0;
+    } else if (wid == 1) {
+      int base = 0;
       for (int j0 = 0; j0 < COLS - 1; j0 += 32) {
         const int j = j0 + lane;
-        const bool pr = j < COLS - 1 && sh.nonb[j] >= n && sh.nonb[j] < n + m;
+        const int v = j < COLS - 1 ? sh.nonb[j] : 0;
+        const bool pr = j < COLS - 1 && v >= n && v < n + m;
         const unsigned mk = __ballot_sync(kFull, pr);
-        if (pr) sh.ns[base + __popc(mk & ((1u << lane) - 1u))] = j;
+        if (pr) {
+          const int q = base + __popc(mk & ((1u << lane) - 1u));
+          sh.ns[q] = j;
+          sh.kr[q] = v - n;
+        }
         base += __popc(mk);
       }
       if (lane == 0) sh.nns = base;
@@ -421,13 +629,16 @@ __global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauPa
       sh.sp[i] = -1;
       sh.yv[i] = 0.0;
       sh.rhof[i] = 0.f;
+      sh.dyf[i] = 0.f;
       sh.xb[i] = i < m ? double(sh.rhs[i]) : 0.0;
     }
+    for (int j = tid; j < COLS; j += NT) sh.posx[j] = -1;
     __syncthreads();
     const int nsb = sh.nsb, nns = sh.nns;
     for (int i = tid; i < m; i += NT) {
       const int v = sh.basic[i];
       if (v >= n) sh.sp[v - n] = i;
+      else sh.posx[v] = i;
     }
     if (lane == 31) {
 #pragma unroll
@@ -438,38 +649,109 @@ __global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauPa
       }
     }
     __syncthreads();
-    // FP64 residuals: r = b - [A I]_B x_B (one row per thread) and
-    // rho_t = c_B(t) - (B^T y)_t (structural basic rows, on the other threads).
+    // FP64 dot products (the FP64 unit is the scarce resource here: these two
+    // are the only FP64 loops, m nsb + n nns multiply-adds in all).
+    //   row_dot(i):  sum_q A[i, jb[q]] x[sb[q]]       (A_B x_B, row i)
+    //   col_dot(j):  sum_p A[kr[p], j] y[kr[p]]       ((A^T y)_j over the non-basic slacks)
+    auto row_dot = [&](int i) {
+      double s0 = 0.0;
+      if (dt == LPB_DTYPE_F64) {
+        const double *ar = reinterpret_cast<const double *>(sA) + i * sld;
+#pragma unroll 4
+        for (int q = 0; q < nsb; ++q) s0 = fma(ar[sh.jb[q]], sh.xb[sh.sb[q]], s0);
+      } else {
+        const float *ar = reinterpret_cast<const float *>(sA) + i * sld;
+#pragma unroll 4
+        for (int q = 0; q < nsb; ++q) s0 = fma(double(ar[sh.jb[q]]), sh.xb[sh.sb[q]], s0);
+      }
+      return s0;
+    };
+    auto col_dot = [&](int j) {
+      double s0 = 0.0;
+      if (dt == LPB_DTYPE_F64) {
+        const double *ac = reinterpret_cast<const double *>(sA) + j;
+#pragma unroll 4
+        for (int q = 0; q < nns; ++q) s0 = fma(ac[sh.kr[q] * sld], sh.yv[sh.kr[q]], s0);
+      } else {
+        const float *ac = reinterpret_cast<const float *>(sA) + j;
+#pragma unroll 4
+        for (int q = 0; q < nns; ++q) s0 = fma(double(ac[sh.kr[q] * sld]), sh.yv[sh.kr[q]], s0);
+      }
+      return s0;
+    };
+    // FP32 products of A with small corrections, and the sum of their
+    // magnitudes for the error bound: A is read as hi2f of its high word.
+    auto row_delta = [&](int i, float &mag) {
+      float s0 = 0.f, e0 = 0.f;
+      if (dt == LPB_DTYPE_F64) {
+        const unsigned *ar = reinterpret_cast<const unsigned *>(sA) + 2 * i * sld + 1;
+#pragma unroll 4
+        for (int q = 0; q < nsb; ++q) {
+          const float a = hi2f(ar[2 * sh.jb[q]]), d = sh.dxf[sh.sb[q]];
+          s0 = fmaf(a, d, s0);
+          e0 = fmaf(fabsf(a), fabsf(d), e0);
+        }
+      } else {
+        const float *ar = reinterpret_cast<const float *>(sA) + i * sld;
+#pragma unroll 4
+        for (int q = 0; q < nsb; ++q) {
+          const float a = ar[sh.jb[q]], d = sh.dxf[sh.sb[q]];
+          s0 = fmaf(a, d, s0);
+          e0 = fmaf(fabsf(a), fabsf(d), e0);
+        }
+      }
+      mag = e0;
+      return s0;
+    };
+    auto col_delta = [&](int j, float &mag) {
+      float s0 = 0.f, e0 = 0.f;
+      if (dt == LPB_DTYPE_F64) {
+        const unsigned *ac = reinterpret_cast<const unsigned *>(sA) + 2 * j + 1;
+#pragma unroll 4
+        for (int q = 0; q < nns; ++q) {
+          const int k = sh.kr[q];
+          const float a = hi2f(ac[2 * k * sld]), d = sh.dyf[k];
+          s0 = fmaf(a, d, s0);
+          e0 = fmaf(fabsf(a), fabsf(d), e0);
+        }
+      } else {
+        const float *ac = reinterpret_cast<const float *>(sA) + j;
+#pragma unroll 4
+        for (int q = 0; q < nns; ++q) {
+          const int k = sh.kr[q];
+          const float a = ac[k * sld], d = sh.dyf[k];
+          s0 = fmaf(a, d, s0);
+          e0 = fmaf(fabsf(a), fabsf(d), e0);
+        }
+      }
+      mag = e0;
+      return s0;
+    };
+    // Residuals in FP64: sax = b - A x and r = sax - x_slack (rows, on the low
+    // threads); the reduced costs d = A^T y - c of every column (high
+    // threads), whose negatives on the basic structurals are the dual residual.
     for (int i = tid; i < m; i += NT) {
-      double r = ld_in(P.B.b, boff + i, dt);
-#pragma unroll 4
-      for (int q = 0; q < nsb; ++q) {
-        const int t = sh.sb[q];
-        r = fma(-a_at<double>(sA, dt, i * sld + sh.basic[t]), sh.xb[t], r);
-      }
-      if (sh.sp[i] >= 0) r -= sh.xb[sh.sp[i]];
+      const double ax = vin(sh.bin, i, dt) - row_dot(i);
+      const double r = sh.sp[i] >= 0 ? ax - sh.xb[sh.sp[i]] : ax;
+      sh.sax[i] = ax;
       sh.rr[i] = r;
+      sh.rrf[i] = float(r);
     }
-    for (int q = NT - 1 - tid; q < nsb; q += NT) {
-      const int t = sh.sb[q], j = sh.basic[t];
-      double r = ld_in(P.B.c, coff + j, dt);
-#pragma unroll 4
-      for (int p2 = 0; p2 < nns; ++p2) {
-        const int k = sh.nonb[sh.ns[p2]] - n;
-        r = fma(-a_at<double>(sA, dt, k * sld + j), sh.yv[k], r);
-      }
-      sh.rho[t] = r;
-      sh.rhof[t] = float(r);
+    for (int j = NT - 1 - tid; j < n; j += NT) {
+      const double d = col_dot(j) - vin(sh.cin, j, dt);
+      sh.dj[j] = d;
+      if (sh.posx[j] >= 0) sh.rhof[sh.posx[j]] = float(-d);
     }
     __syncthreads();
     // Corrections with the FP32 basis inverse held in registers: its column for
     // slack k is the tableau column of k when k is non-basic, else a unit vector.
     {
+      constexpr int CP = pow2_at_least(C);
       float coef[C];
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         const int v = sh.nonb[wid + W * c];
-        coef[c] = (c < C - 1 || wid < W - 1) && v >= n && v < n + m ? float(sh.rr[v - n]) : 0.f;
+        coef[c] = (c < C - 1 || wid < W - 1) && v >= n && v < n + m ? sh.rrf[v - n] : 0.f;
       }
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -481,15 +763,25 @@ __global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauPa
       float rf[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) rf[r] = sh.rhof[lane + 32 * r];
+      float dy[CP];
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const int v = sh.nonb[wid + W * c];
-        if ((c < C - 1 || wid < W - 1) && v >= n && v < n + m) {   // warp-uniform
-          float s = 0.f;
+      for (int c = 0; c < CP; ++c) {
+        float s = 0.f;
+        if (c < C) {
 #pragma unroll
           for (int r = 0; r < R; ++r) s = fmaf(T[r][c], rf[r], s);
-          s = warp_sum(s);
-          if (lane == 0) sh.yv[v - n] += double(s);
+        }
+        dy[c] = s;
+      }
+      // Column sums across the lanes; lane l ends with column l / (32 / CP),
+      // and the first lane of each group applies it to y.
+      const float tot = reduce_scatter<CP>(dy, lane);
+      const int c = lane / (32 / CP);
+      if (lane % (32 / CP) == 0 && c < C && (c < C - 1 || wid < W - 1)) {
+        const int v = sh.nonb[wid + W * c];
+        if (v >= n && v < n + m) {
+          sh.yv[v - n] += double(tot);
+          sh.dyf[v - n] = tot;
         }
       }
     }
@@ -498,70 +790,61 @@ __global__ void __launch_bounds__(W * 32, (W <= 4 ? 3 : 2)) reg_kernel(TableauPa
       float s = 0.f;
 #pragma unroll
       for (int w = 0; w < W; ++w) s += sh.part[w][t];
-      double dx = double(s);
       const int v = sh.basic[t];
-      if (v >= n) dx += sh.rr[v - n];
+      const double dx = v >= n ? double(s) + sh.rr[v - n] : double(s);
       sh.xb[t] += dx;
+      sh.dxf[t] = v < n ? float(dx) : 0.f;         // the structural part of the correction
     }
     __syncthreads();
-    // FP64 KKT certificate of the pair that is written out (x: the structural
-    // part of x_B; y: the slack duals): x >= 0, A x <= b, y >= 0, A^T y >= c and
-    // c^T x = b^T y, each to tol scaled by the data.  Rows on the low threads,
-    // columns on the high ones.
+    // KKT certificate of the pair that is written out (x: the structural part
+    // of x_B; y: the slack duals): x >= 0, A x <= b, y >= 0, A^T y >= c and
+    // c^T x = b^T y, each to tol scaled by the data.  b - A x and A^T y - c at
+    // the corrected point are the FP64 values above plus FP32 products with
+    // the corrections, whose rounding (and the 2^-20 truncation of A) is
+    // bounded by 2^-15 times the sum of the products' magnitudes.
     const double tol = P.feas_tol, tp = tol * (1.0 + bmax), td = tol * (1.0 + cmax);
+    constexpr float kDeltaErr = 1.f / 32768.f;
     int fail = 0;
-    double cx = 0.0, by = 0.0;
-    for (int q = tid; q < nsb; q += NT) {
-      const int t = sh.sb[q];
-      fail |= !(sh.xb[t] >= -tp);
-      cx = fma(ld_in(P.B.c, coff + sh.basic[t], dt), sh.xb[t], cx);
-    }
-    for (int p2 = tid; p2 < nns; p2 += NT) {
-      const int k = sh.nonb[sh.ns[p2]] - n;
-      fail |= !(sh.yv[k] >= -td);
-      by = fma(ld_in(P.B.b, boff + k, dt), sh.yv[k], by);
-    }
+    for (int q = tid; q < nsb; q += NT) fail |= !(sh.xb[sh.sb[q]] >= -tp);
+    for (int p2 = tid; p2 < nns; p2 += NT) fail |= !(sh.yv[sh.kr[p2]] >= -td);
     for (int i = tid; i < m; i += NT) {                 // slack b_i - A_i x of every row
-      double s = ld_in(P.B.b, boff + i, dt);
-#pragma unroll 4
-      for (int q = 0; q < nsb; ++q) s = fma(-a_at<double>(sA, dt, i * sld + sh.basic[sh.sb[q]]), sh.xb[sh.sb[q]], s);
-      fail |= !(s >= -tp);
+      float mag;
+      const float dl = row_delta(i, mag);
+      fail |= !(sh.sax[i] - double(dl + kDeltaErr * mag) >= -tp);
     }
     for (int j = NT - 1 - tid; j < n; j += NT) {        // reduced cost A_j^T y - c_j of every column
-      double d = -ld_in(P.B.c, coff + j, dt);
-#pragma unroll 4
-      for (int p2 = 0; p2 < nns; ++p2) {
-        const int k = sh.nonb[sh.ns[p2]] - n;
-        d = fma(a_at<double>(sA, dt, k * sld + j), sh.yv[k], d);
-      }
-      fail |= !(d >= -td);
+      float mag;
+      const float dl = col_delta(j, mag);
+      fail |= !(sh.dj[j] + double(dl - kDeltaErr * mag) >= -td);
     }
-    cx = warp_sum(cx);
-    by = warp_sum(by);
-    if (lane == 0) { sh.red[0][wid] = cx; sh.red[1][wid] = by; }
+    // c^T x in warp 0 and b^T y in warp 1 (FP64).
+    if (wid == 0) {
+      double cx = 0.0;
+      for (int q = lane; q < nsb; q += 32) cx = fma(vin(sh.cin, sh.jb[q], dt), sh.xb[sh.sb[q]], cx);
+      cx = warp_sum(cx);
+      if (lane == 0) sh.red[0][0] = cx;
+    } else if (wid == 1) {
+      double by = 0.0;
+      for (int p2 = lane; p2 < nns; p2 += 32) by = fma(vin(sh.bin, sh.kr[p2], dt), sh.yv[sh.kr[p2]], by);
+      by = warp_sum(by);
+      if (lane == 0) sh.red[1][0] = by;
+    }
     fail = __syncthreads_or(fail);
-    cx = 0.0;
-    by = 0.0;
-#pragma unroll
-    for (int w = 0; w < W; ++w) { cx += sh.red[0][w]; by += sh.red[1][w]; }
-    fail |= !(fabs(cx - by) <= tol * (1.0 + fabs(cx)));
     if (bp) for (int i = tid; i < m; i += NT) bp[i] = sh.basic[i];
-    if (fail) {
-      if (tid == 0) {
+    if (!fail) {       // written now; a gap failure below sends the LP to the re-solve, which rewrites them
+      for (int j = tid; j < n; j += NT) P.R.x[coff + j] = sh.posx[j] >= 0 ? sh.xb[sh.posx[j]] : 0.0;
+      if (P.R.y) for (int k = tid; k < m; k += NT) P.R.y[boff + k] = sh.yv[k];
+    }
+    if (tid == 0) {
+      const double cx = sh.red[0][0], by = sh.red[1][0];
+      if (!fail && fabs(cx - by) <= tol * (1.0 + fabs(cx))) {
+        P.R.status[lp] = LPB_OPTIMAL;
+        P.R.obj[lp] = cx;
+      } else {
         P.R.status[lp] = STATUS_PENDING;
-        if (P.R.iters) P.R.iters[lp] = iters;
         list_push(P.resolve_items, P.resolve_count, P.list_cap, lp, P.err);
       }
-    } else {
-      for (int j = tid; j < n; j += NT) P.R.x[coff + j] = 0.0;
-      __syncthreads();
-      for (int q = tid; q < nsb; q += NT) P.R.x[coff + sh.basic[sh.sb[q]]] = sh.xb[sh.sb[q]];
-      if (P.R.y) for (int k = tid; k < m; k += NT) P.R.y[boff + k] = sh.yv[k];
-      if (tid == 0) {
-        P.R.status[lp] = LPB_OPTIMAL;
-        if (P.R.iters) P.R.iters[lp] = iters;
-        P.R.obj[lp] = cx;
-      }
+      if (P.R.iters) P.R.iters[lp] = iters;
     }
     __syncthreads();
   }
@@ -583,7 +866,8 @@ const RegConfig kRegConfigs[] = {
 constexpr int kNumReg = int(sizeof(kRegConfigs) / sizeof(kRegConfigs[0]));
 
 size_t reg_smem_bytes(int cfg, int max_m, int max_n, int dtype) {
-  return kRegConfigs[cfg].fixed + size_t(max_m) * size_t(a_stride(max_n)) * (dtype == LPB_DTYPE_F64 ? 8 : 4);
+  const int es = dtype == LPB_DTYPE_F64 ? 8 : 4;
+  return kRegConfigs[cfg].fixed + size_t(max_m) * size_t(a_stride(max_n, es)) * es;
 }
 
 }  // namespace
