@@ -105,7 +105,7 @@ typedef struct {
   double feas_tol;           /* Phase I / verification tolerance [1e-9] */
   int32_t keep_basis_inverse;/* keep what lpb_solve_backward needs in ws [0] */
   int32_t kernel;            /* lpb_kernel: force a kernel class [LPB_KERNEL_AUTO] */
-  int32_t threads;           /* threads per CTA of the tableau kernel [auto] */
+  int32_t threads;           /* threads per CTA of the tableau kernel, a multiple of 32 up to 1024 [auto] */
   int32_t reg_warps;         /* warps per LP of the register kernel, 4 or 8 [autotuned, else 8] */
 } lpb_options;
 
@@ -158,8 +158,9 @@ lpb_err lpb_hyperbox(lpb_handle *handle, int64_t count, int32_t n, int32_t dtype
 
 /* Autotuner.  Picks, for batches shaped like `batch` (same max_m, max_n,
  * dtype and precision), the fastest schedule among: warps per LP of the
- * register kernel (4 or 8), threads per CTA of the tableau kernel (128 or
- * 256) and its placement (shared memory when it fits, or L2-resident slots).
+ * register kernel (4 or 8), threads per CTA of the tableau kernel (automatic,
+ * 256, 512 or 1024) and its placement (shared memory when it fits, or
+ * L2-resident slots).
  * If `table_path` (may be NULL) holds an entry for this shape, that entry is
  * loaded and nothing is timed; otherwise every candidate solves `batch` into
  * `result` on `stream` (one warm-up and two timed runs each, CUDA events),

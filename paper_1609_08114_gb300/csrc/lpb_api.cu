@@ -65,7 +65,7 @@ struct Pass {
   int list = LIST_ALL, cls = 0;
   int lim_m = 0, lim_n = 0;  // size bounds of the launch
   int group = 0;             // timing group: 0 first solve, 1 Phase-I pass, 2 FP64 re-solve
-  size_t smem = 0, slot_bytes = 0;
+  size_t smem = 0, slot_bytes = 0, tab_smem = 0;
 };
 
 constexpr int kMaxPasses = kMaxClasses + 2;
@@ -83,14 +83,27 @@ struct Plan {
   double eps_p = 0, eps_d = 0, feas_tol = 0;
 };
 
-int auto_threads(int max_m, int max_n) {
-  int t = (max_m > max_n ? max_m : max_n);
-  t = (t + 31) & ~31;
+// Threads per CTA of the tableau kernel: about 1024 threads per SM (512 for
+// FP64, whose update is bound by the FP64 pipe and whose per-warp divisions
+// cost more with more warps) over the CTAs that fit by shared memory, and no
+// more than one thread per 8 tableau elements for small LPs.  The kernel is compiled for up to 1024 threads of
+// at most 64 registers, so 1024 threads fill the register file.
+int auto_threads(int eb, int rows, int cols, size_t smem) {
+  int ctas = int(size_t(232448) / (smem + 1024));
+  if (ctas < 1) ctas = 1;
+  if (ctas > 8) ctas = 8;
+  int t = (eb == 8 ? 512 : 1024) / ctas;
+  const long long per8 = (static_cast<long long>(rows) * cols / 8 + 31) & ~31LL;
+  if (per8 < t) t = int(per8);
+  t &= ~31;
   if (t < 64) t = 64;
-  if (t > 256) t = 256;
   return t;
 }
 
+// A pass of the tableau kernel.  Its tableau rows go to shared memory as far
+// as they fit (all of them for the SMEM class), the rest to a per-CTA slot of
+// the workspace, sized so that the slots of all CTAs stay within about 3/4 of
+// L2; LPB_KERNEL_GMEM puts every row in the slot.
 lpb_err make_pass(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o, bool fp64, int kcap,
                   int mode, Pass *p) {
   const int eb = fp64 ? 8 : 4;
@@ -98,29 +111,31 @@ lpb_err make_pass(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   p->fp64 = fp64;
   p->kcap = kcap;
   p->mode = mode;
-  p->threads = o->threads > 0 ? o->threads : auto_threads(b->max_m, b->max_n);
-  if (p->threads < 32 || p->threads > 512 || (p->threads & 31)) return LPB_EINVAL;
-  const size_t smem_s = tableau_smem_bytes(eb, false, b->max_m, b->max_n, kcap, p->threads, refine);
-  const bool want_gmem = o->kernel == LPB_KERNEL_GMEM || smem_s > d.smem_optin;
-  if (o->kernel == LPB_KERNEL_SMEM && smem_s > d.smem_optin) return LPB_EUNSUPPORTED;
+  const size_t fixed = tableau_fixed_bytes(eb, b->max_m, b->max_n, kcap, refine);
+  const size_t rowb = tableau_row_bytes(eb, b->max_n, kcap);
+  const size_t rows = size_t(b->max_m) + 2;
+  // Leave room for the kernel's static shared memory.
+  const size_t budget = d.smem_optin > 2048 ? d.smem_optin - 2048 : 0;
+  if (fixed + 16 > budget) return LPB_EUNSUPPORTED;
+  size_t fit_rows = (budget - fixed) / rowb;
+  if (fit_rows > rows) fit_rows = rows;
+  if (o->kernel == LPB_KERNEL_SMEM && fit_rows < rows) return LPB_EUNSUPPORTED;
+  if (o->kernel == LPB_KERNEL_GMEM) fit_rows = 0;
+  p->tab_smem = fit_rows * rowb;
+  p->slot_bytes = ((rows - fit_rows) * rowb + 127) & ~size_t(127);
+  p->gmem = p->slot_bytes > 0;
+  p->smem = fixed + p->tab_smem;
+  if (p->smem < 16) p->smem = 16;
+  p->threads = o->threads > 0 ? o->threads : auto_threads(eb, int(rows), int(rowb / eb), p->smem);
+  if (p->threads < 32 || p->threads > 1024 || (p->threads & 31)) return LPB_EINVAL;
   int occ = 0;
-  if (!want_gmem) {
-    p->gmem = false;
-    p->smem = smem_s;
-    if (tableau_max_ctas_per_sm(eb, false, p->threads, p->smem, &occ) != cudaSuccess) return LPB_ECUDA;
-    if (occ < 1) return LPB_EUNSUPPORTED;
-    p->grid = occ * d.sms;
-  } else {
-    p->gmem = true;
-    p->smem = tableau_smem_bytes(eb, true, b->max_m, b->max_n, kcap, p->threads, refine);
-    if (p->smem > d.smem_optin) return LPB_EUNSUPPORTED;
-    p->slot_bytes = tableau_slot_bytes(eb, b->max_m, b->max_n, kcap);
-    if (tableau_max_ctas_per_sm(eb, true, p->threads, p->smem, &occ) != cudaSuccess) return LPB_ECUDA;
-    if (occ < 1) return LPB_EUNSUPPORTED;
-    // Keep the in-flight tableaux within about 3/4 of L2, but use every SM.
+  if (tableau_max_ctas_per_sm(eb, p->threads, p->smem, &occ) != cudaSuccess) return LPB_ECUDA;
+  if (occ < 1) return LPB_EUNSUPPORTED;
+  p->grid = occ * d.sms;
+  if (p->gmem) {
     size_t fit = (d.l2_bytes * 3 / 4) / p->slot_bytes;
     if (fit < size_t(d.sms)) fit = size_t(d.sms);
-    p->grid = int(fit < size_t(occ) * d.sms ? fit : size_t(occ) * d.sms);
+    if (fit < size_t(p->grid)) p->grid = int(fit);
   }
   if (p->grid > b->count) p->grid = b->count > 0 ? b->count : 1;
   return LPB_OK;
@@ -342,6 +357,7 @@ lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_ba
     p.kcap = ps.kcap;
     p.mode = ps.mode;
     p.slot_bytes = ps.slot_bytes;
+    p.tab_smem = ps.tab_smem;
     p.lim_m = ps.lim_m;
     p.lim_n = ps.lim_n;
     p.queue = queues + i;
@@ -363,7 +379,7 @@ lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_ba
         break;
     }
     const cudaError_t ce = ps.reg >= 0 ? launch_reg(p, ps.reg, ps.grid, ps.smem, s)
-                                       : launch_tableau(p, ps.fp64, ps.gmem, ps.grid, ps.threads, ps.smem, s);
+                                       : launch_tableau(p, ps.fp64, ps.grid, ps.threads, ps.smem, s);
     if (ce != cudaSuccess) return LPB_ECUDA;
     if (kernels) *kernels += 1;
   }
@@ -512,8 +528,9 @@ lpb_err lpb_autotune(lpb_handle *h, const lpb_batch *b, const lpb_options *o, co
   struct Cand { int kernel, threads, reg_warps; };
   const bool fp32 = o->prec != LPB_FP64;
   const Cand cands[] = {
-      {LPB_KERNEL_AUTO, 0, fp32 ? 8 : 0}, {LPB_KERNEL_AUTO, 0, fp32 ? 4 : 0}, {LPB_KERNEL_AUTO, 128, fp32 ? 8 : 0},
-      {LPB_KERNEL_AUTO, 256, fp32 ? 8 : 0}, {LPB_KERNEL_SMEM, 0, 0}, {LPB_KERNEL_GMEM, 0, 0}};
+      {LPB_KERNEL_AUTO, 0, fp32 ? 8 : 0}, {LPB_KERNEL_AUTO, 0, fp32 ? 4 : 0}, {LPB_KERNEL_AUTO, 256, fp32 ? 8 : 0},
+      {LPB_KERNEL_AUTO, 512, fp32 ? 8 : 0}, {LPB_KERNEL_AUTO, 1024, fp32 ? 8 : 0}, {LPB_KERNEL_SMEM, 0, 0},
+      {LPB_KERNEL_GMEM, 0, 0}};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return LPB_ECUDA;

@@ -142,9 +142,10 @@ __device__ __forceinline__ void block_argmin(T &v, int &k, T *bv, int *bk) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (lane == 0) { bv[w] = v; bk[w] = k; }
   __syncthreads();
-  v = bv[0];
-  k = bk[0];
-  for (int i = 1; i < nw; ++i) keep_better(v, k, bv[i], bk[i]);
+  // Lanes past the last warp repeat slot 0, which cannot change the minimum.
+  v = bv[lane < nw ? lane : 0];
+  k = bk[lane < nw ? lane : 0];
+  warp_argmin(v, k);
 }
 
 template <typename T>
@@ -220,8 +221,9 @@ struct TableauParams {
   int32_t *bbuf;               // basis output (and warm-start input): packed like b when
   int bpacked;                 //   bpacked, else max_m entries per LP
   int warm;                    // start from the basis in bbuf (FP64 re-solve)
-  void *slots;                 // GMEM class: per-CTA tableau slots
+  void *slots;                 // per-CTA slots for the tableau rows beyond shared memory
   size_t slot_bytes;
+  size_t tab_smem;             // bytes of tableau rows in shared memory (tableau kernel)
   int lim_m, lim_n;            // size bounds of this launch (register kernel: its class)
   int kcap;                    // artificial columns this launch can hold
   int mode;                    // Mode
@@ -263,12 +265,15 @@ struct HyperboxParams {
 };
 
 // Launchers (simplex_tableau.cu, hyperbox.cu).
-size_t tableau_smem_bytes(int elem_bytes, bool gmem, int max_m, int max_n, int kcap, int threads,
-                          bool refine);
-size_t tableau_slot_bytes(int elem_bytes, int max_m, int max_n, int kcap);
-cudaError_t tableau_max_ctas_per_sm(int elem_bytes, bool gmem, int threads, size_t smem, int *ctas);
-cudaError_t launch_tableau(const TableauParams &p, bool fp64, bool gmem, int grid, int threads,
-                           size_t smem, cudaStream_t s);
+// Shared-memory bytes of the tableau kernel's buffers (everything but rows),
+// and the bytes of one tableau row, for LPs up to max_m x max_n with up to
+// kcap negated rows.  A launch holds `tab_smem` bytes of rows in shared
+// memory after those buffers and the rest of each tableau in a slot of
+// `slot_bytes` per CTA.
+size_t tableau_fixed_bytes(int elem_bytes, int max_m, int max_n, int kcap, bool refine);
+size_t tableau_row_bytes(int elem_bytes, int max_n, int kcap);
+cudaError_t tableau_max_ctas_per_sm(int elem_bytes, int threads, size_t smem, int *ctas);
+cudaError_t launch_tableau(const TableauParams &p, bool fp64, int grid, int threads, size_t smem, cudaStream_t s);
 // Register-resident FP32 kernel (simplex_reg.cu): configuration index for
 // (max_m, max_n) or -1, its occupancy, and its launch.  It defers to the
 // defer list every LP it does not take (Phase I, sizes, non-finite data).

@@ -9,17 +9,23 @@
 //    the right-hand side.  The paper's layout (Section 3.1, Fig. 1) keeps the
 //    basic columns too; they are identity columns and carry no information, so
 //    the compact form does the same pivots on about half the elements.
-//  * Storage: shared memory when the tableau fits (SMEM class), else a per-CTA
-//    slot of the workspace that stays resident in L2 (GMEM class).  Rows are
-//    contiguous with an odd leading dimension so column reads are free of bank
-//    conflicts; warps own rows and lanes own columns in the pivot update.
-//  * Steps 1 and 2 are (value, key) arg-min reductions: warp shuffles, then one
-//    slot per warp in shared memory (replacing the Data/Indices arrays and
-//    sequential-addressing tree of Section 4.2).  Ineligible ratios are +inf
-//    (the INT_MAX sentinel of Section 4.2).  Ties go to the lowest variable
-//    index (Step 1) and the lowest basic-variable index (Step 2).
-//  * Step 3 (Section 4.3) is a rank-1 update with the pivot column, pre-scaled
-//    by 1/pivot, broadcast from shared memory.
+//  * Storage: the leading rows live in shared memory, as many as fit; the rest
+//    (none for most LPs) in a per-CTA workspace slot that stays in L2.  Rows
+//    have an odd leading dimension, so the column reads of Step 2 are free of
+//    bank conflicts.
+//  * Work split: warp w owns a contiguous block of rows; lanes own columns.
+//    One pivot takes two block barriers.  Before the first, every warp runs
+//    Step 2 on its own rows (a warp arg-min, one slot per warp) and the
+//    reciprocal of its best pivot.  After it, every warp reduces the slots,
+//    keeps the pivot row in registers and applies the rank-1 update of Step 3
+//    to its rows; the warp owning the pivot row writes the scaled row to a
+//    buffer, and the warp owning the objective row runs Step 1 for the next
+//    pivot on its freshly updated row.  After the second barrier the owner
+//    copies the scaled pivot row into place.  The Data/Indices arrays and the
+//    sequential-addressing reduction of Section 4.2 become warp shuffles;
+//    ineligible ratios are +inf (the INT_MAX sentinel of Section 4.2).  Ties
+//    go to the lowest variable index (Step 1) and the lowest basic-variable
+//    index (Step 2).
 //  * Work: a persistent grid pops LPs from an atomic queue, so LPs with more
 //    pivots do not hold up a wave.
 //  * FP32 mode with refinement: after an FP32 solve the basis inverse sits in
@@ -27,34 +33,44 @@
 //    x_B = B^{-1} b and y = B^{-T} c_B with FP64 residuals follows, then an FP64
 //    primal/dual feasibility and duality-gap check.  LPs that fail are queued
 //    for an FP64 re-solve warm-started from their FP32 basis.
+#include <type_traits>
+
 #include "lpb_internal.cuh"
 
 namespace lpb {
 namespace {
 
-constexpr int kMaxThreads = 512;
+constexpr int kMaxThreads = 1024;
 
 struct Layout {
-  size_t tab, colb, rowb, basic, nonb, redv, redk, ins, xb, rr, yv, rho, sb, ns, sp, total;
+  size_t tab, colb, rowb, basic, nonb, redv, redk, rcp, redf, sel, ins, xb, rr, yv, rho, sb, ns, sp, dj, jq, kq, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline int tab_ld(int n, int k) { return (n + k + 1) | 1; }
+// Row length in elements: whole 16-byte vectors, so that the update moves
+// rows with vector accesses.  The padding columns stay zero under pivoting.
+__host__ __device__ inline int tab_ld(int n, int k, int eb) {
+  const int per = 16 / eb;
+  return (n + k + 1 + per - 1) / per * per;
+}
 
-__host__ __device__ inline Layout make_layout(int eb, bool gmem, int max_m, int max_n, int kcap,
-                                              bool refine) {
+// Dynamic shared memory: `tab` bytes of tableau rows, then the buffers.
+__host__ __device__ inline Layout make_layout(int eb, size_t tab, int max_m, int max_n, int kcap, bool refine) {
   Layout L{};
-  const size_t ld = size_t(tab_ld(max_n, kcap));
+  const size_t ld = size_t(tab_ld(max_n, kcap, eb));
   const size_t rows = size_t(max_m) + 2;
   size_t o = 0;
-  L.tab = o;   o = align16(o + (gmem ? 0 : rows * ld * eb));
+  L.tab = o;   o = align16(o + tab);
   L.colb = o;  o = align16(o + rows * eb);
   L.rowb = o;  o = align16(o + ld * eb);
   L.basic = o; o = align16(o + size_t(max_m) * 4);
   L.nonb = o;  o = align16(o + ld * 4);
   L.redv = o;  o = align16(o + 64 * size_t(eb));
   L.redk = o;  o = align16(o + 64 * 4);
+  L.rcp = o;   o = align16(o + 33 * size_t(eb));
+  L.redf = o;  o = align16(o + 32 * 4);
+  L.sel = o;   o = align16(o + 4 * 4);
   L.ins = o;   o = align16(o + size_t(max_n) + 2 * size_t(max_m) + 1);
   if (refine) {
     L.xb = o;  o = align16(o + size_t(max_m) * 8);
@@ -64,6 +80,9 @@ __host__ __device__ inline Layout make_layout(int eb, bool gmem, int max_m, int 
     L.sb = o;  o = align16(o + size_t(max_m) * 4);
     L.ns = o;  o = align16(o + size_t(max_m) * 4);
     L.sp = o;  o = align16(o + size_t(max_m) * 4);
+    L.dj = o;  o = align16(o + size_t(max_n) * 8);
+    L.jq = o;  o = align16(o + size_t(max_m) * 4);
+    L.kq = o;  o = align16(o + size_t(max_m) * 4);
   }
   L.total = o;
   return L;
@@ -76,136 +95,305 @@ template <> __device__ __forceinline__ double pos_inf<double>() { return __longl
 // Per-LP working state shared by the helper routines.
 template <typename T>
 struct Tab {
-  T *t;           // tableau, row-major with leading dimension ld
+  T *ts;          // rows 0..rs-1 in shared memory (leading dimension ld)
+  T *tg;          // rows rs.. in the CTA's workspace slot
+  int rs;
   T *colb, *rowb;
   int *basic, *nonb;
   T *redv;
   int *redk;
+  T *rcp;         // per-warp reciprocal of the warp's best pivot (Step 2)
+  float *redf;    // per-warp smallest FP32 ratio (FP64 Step 2)
+  int *sel;       // Step 1 result for the next pivot: sel[0] = key or INT_MAX
   unsigned char *ins;
   int m, n, k, nc, ld;   // nc = n + k non-RHS columns; column nc is the RHS
   int nm;                // variables >= nm are artificial
-  bool gmem;             // the tableau is a workspace slot (L2), not shared memory
+  __device__ __forceinline__ T *row(int i) const {
+    return i < rs ? ts + size_t(i) * ld : tg + size_t(i - rs) * ld;
+  }
+  __device__ __forceinline__ T &at(int i, int j) const { return row(i)[j]; }
 };
 
-// Step 3: pivot on (l, e), updating rows 0..rows-1.
+// Rows [r0, r1) owned by the calling warp when `rows` rows are split into
+// contiguous blocks, one per warp.
+__device__ __forceinline__ void own_rows(int rows, int &r0, int &r1) {
+  const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+  const int per = (rows + nw - 1) / nw;
+  r0 = w * per;
+  r1 = min(rows, r0 + per);
+}
+
+// 16-byte vectors of the tableau's element type.
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+  using type = float4;
+  static constexpr int N = 4;
+};
+template <> struct Vec<double> {
+  using type = double2;
+  static constexpr int N = 2;
+};
+// One vector of a row under Step 3: x - f pr, with component ce (the pivot
+// column, -1 if none) set to -f; and the scaled pivot row pr * rp with
+// component ce set to rp.  Vectors pass by value (taking a vector's address
+// would move it to local memory).
+__device__ __forceinline__ float4 upd_vec(float4 x, float4 pr, float nf, int ce) {
+  x.x = ce == 0 ? nf : fmaf(nf, pr.x, x.x);
+  x.y = ce == 1 ? nf : fmaf(nf, pr.y, x.y);
+  x.z = ce == 2 ? nf : fmaf(nf, pr.z, x.z);
+  x.w = ce == 3 ? nf : fmaf(nf, pr.w, x.w);
+  return x;
+}
+__device__ __forceinline__ double2 upd_vec(double2 x, double2 pr, double nf, int ce) {
+  x.x = ce == 0 ? nf : fma(nf, pr.x, x.x);
+  x.y = ce == 1 ? nf : fma(nf, pr.y, x.y);
+  return x;
+}
+__device__ __forceinline__ float4 scale_vec(float4 pr, float rp, int ce) {
+  return make_float4(ce == 0 ? rp : pr.x * rp, ce == 1 ? rp : pr.y * rp, ce == 2 ? rp : pr.z * rp,
+                     ce == 3 ? rp : pr.w * rp);
+}
+__device__ __forceinline__ double2 scale_vec(double2 pr, double rp, int ce) {
+  return make_double2(ce == 0 ? rp : pr.x * rp, ce == 1 ? rp : pr.y * rp);
+}
+
+// Step 3 on the calling warp's rows: with rp = 1 / t_le, every row i != l
+// becomes row_i - (t_ie rp) row_l and its column e -t_ie rp; the warp owning
+// row l writes the scaled row (rp at column e) to S.rowb instead of row l, so
+// that other warps can still read the old row; pivot_finish() copies it.
+// Lanes own 16-byte vectors of columns; a lane keeps its vector of the pivot
+// row in registers and loads kQ rows of its column before it stores any, so a
+// batch costs one round trip to shared memory or L2.
+template <typename T, int kQ>
+__device__ __forceinline__ void pivot_update(const Tab<T> &S_, int rows, int l, int e, T rp) {
+  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
+  using V = typename Vec<T>::type;
+  constexpr int NV = Vec<T>::N;
+  const int lane = threadIdx.x & 31;
+  int r0, r1;
+  own_rows(rows, r0, r1);
+  for (int i = r0 + lane; i < r1; i += 32) S.colb[i] = i == l ? T(0) : S.at(i, e) * rp;
+  __syncwarp();
+  if (r0 >= r1) return;
+  const bool own_l = l >= r0 && l < r1;
+  const int nv = (S.nc + NV) / NV;        // vectors holding columns 0..nc
+  const int ev = e / NV, ec = e % NV;
+  const V *prow = reinterpret_cast<const V *>(S.row(l));
+  V *rowb = reinterpret_cast<V *>(S.rowb);
+  for (int jv = lane; jv < nv; jv += 32) {
+    const V pr = prow[jv];
+    const int ce = jv == ev ? ec : -1;
+    if (own_l) rowb[jv] = scale_vec(pr, rp, ce);
+    for (int i0 = r0; i0 < r1; i0 += kQ) {
+      V v[kQ];
+      T f[kQ];
+      V *rw[kQ];
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) {
+        const int i = i0 + q;
+        const bool ok = i < r1 && i != l;
+        f[q] = ok ? S.colb[i] : T(0);
+        rw[q] = reinterpret_cast<V *>(S.row(ok ? i : r0));
+        v[q] = rw[q][jv];                 // row r0 stands in for a skipped row
+      }
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) {
+        const int i = i0 + q;
+        if (i >= r1 || i == l) continue;
+        const V x = upd_vec(v[q], pr, -f[q], ce);
+        rw[q][jv] = x;
+      }
+    }
+  }
+}
+
+// After the barrier that follows pivot_update: the owner of row l copies the
+// scaled pivot row into place.
 template <typename T>
-__device__ void pivot(Tab<T> &S, int rows, int l, int e) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  const int ld = S.ld, nc = S.nc;
-  const T p = S.t[size_t(l) * ld + e];
-  for (int i = tid; i < rows; i += nt) S.colb[i] = S.t[size_t(i) * ld + e] / p;
-  for (int j = tid; j <= nc; j += nt) S.rowb[j] = S.t[size_t(l) * ld + j];
-  if (tid == 0) {
+__device__ __forceinline__ void pivot_finish(const Tab<T> &S_, int rows, int l) {
+  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
+  using V = typename Vec<T>::type;
+  constexpr int NV = Vec<T>::N;
+  int r0, r1;
+  own_rows(rows, r0, r1);
+  if (l >= r0 && l < r1) {
+    V *prow = reinterpret_cast<V *>(S.row(l));       // whole vectors: the padding is scaled zero
+    const V *rb = reinterpret_cast<const V *>(S.rowb);
+    const int nv = (S.nc + NV) / NV;
+    for (int j = threadIdx.x & 31; j < nv; j += 32) prow[j] = rb[j];
+  }
+  __syncwarp();
+}
+
+template <typename T>
+__device__ __forceinline__ void update_any(const Tab<T> &S_, int rows, int l, int e, T rp) {
+  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
+  pivot_update<T, sizeof(T) == 4 ? 4 : 2>(S, rows, l, e, rp);
+}
+
+// A whole pivot on (l, e) for the callers outside the Step 1-3 loop (Phase-I
+// clean-up, warm start, dual simplex): the tableau must be stable on entry.
+template <typename T>
+__device__ __forceinline__ void pivot(const Tab<T> &S_, int rows, int l, int e) {
+  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
+  T rp = T(0);
+  if ((threadIdx.x & 31) == 0) rp = T(1) / S.at(l, e);
+  rp = __shfl_sync(kFull, rp, 0);
+  if (threadIdx.x == 0) {
     const int v = S.basic[l];
     S.basic[l] = S.nonb[e];
     S.nonb[e] = v;
   }
+  update_any(S, rows, l, e, rp);
   __syncthreads();
-  if (!S.gmem) {           // shared-memory tableau: short latencies, plain loop
-    for (int i = wid; i < rows; i += nw) {
-      T *row = S.t + size_t(i) * ld;
-      if (i == l) {
-        for (int j = lane; j <= nc; j += 32) row[j] = (j == e) ? T(1) / p : S.rowb[j] / p;
-      } else {
-        const T f = S.colb[i];
-        for (int j = lane; j <= nc; j += 32) row[j] = (j == e) ? -f : fma(-f, S.rowb[j], row[j]);
-      }
-    }
-    __syncthreads();
-    return;
-  }
-  // Slot tableau in L2: warps own rows, lanes own columns, and each lane loads
-  // kU elements of kR rows before it updates them, so a batch costs one round
-  // trip instead of one per element.
-  constexpr int kR = 2, kU = 4;
-  for (int i0 = wid; i0 < rows; i0 += nw * kR) {
-    for (int j0 = lane; j0 <= nc; j0 += 32 * kU) {
-      T v[kR][kU], rb[kU];
-#pragma unroll
-      for (int u = 0; u < kU; ++u) {
-        const int j = j0 + 32 * u;
-        rb[u] = j <= nc ? S.rowb[j] : T(0);
-#pragma unroll
-        for (int q = 0; q < kR; ++q) {
-          const int i = i0 + q * nw;
-          v[q][u] = (i < rows && j <= nc) ? S.t[size_t(i) * ld + j] : T(0);
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < kR; ++q) {
-        const int i = i0 + q * nw;
-        if (i >= rows) continue;
-        T *row = S.t + size_t(i) * ld;
-        const T f = S.colb[i];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-          const int j = j0 + 32 * u;
-          if (j > nc) continue;
-          if (i == l) row[j] = (j == e) ? T(1) / p : rb[u] / p;
-          else row[j] = (j == e) ? -f : fma(-f, rb[u], v[q][u]);
-        }
-      }
-    }
-  }
+  pivot_finish(S, rows, l);
   __syncthreads();
+}
+
+// Step 1 over objective row `orow` in one warp (every lane gets the result):
+// the most negative reduced cost below -eps_d over enterable columns (the
+// lowest variable index under Bland's rule).  Column `ecol` is taken to hold
+// variable `evar` (a pivot whose swap of nonb may not be visible yet).
+template <typename T>
+__device__ __forceinline__ void step1_warp(const Tab<T> &S_, int orow, bool bland, T eps_d, int ecol, int evar,
+                                           T &v, int &key) {
+  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
+  const T *r = S.row(orow);
+  v = pos_inf<T>();
+  key = INT_MAX;
+  for (int j = threadIdx.x & 31; j < S.nc; j += 32) {
+    const int var = j == ecol ? evar : S.nonb[j];
+    if (var >= S.nm) continue;
+    const T rj = r[j];
+    if (rj < -eps_d) keep_better(v, key, bland ? T(0) : rj, (var << kIdxBits) | j);
+  }
+  warp_argmin(v, key);
 }
 
 // Steps 1-3 on objective row `orow` until a halt condition (Section 3.1).
 // Phase 1 also ratio-tests rows whose basic variable is artificial; phase 2
 // skips them (they are redundant rows left after Phase I).
 template <typename T>
-__device__ int run_phase(Tab<T> &S, int orow, int rows, int phase, int &iters, int max_iter,
+__device__ __forceinline__ int run_phase(const Tab<T> &S_, int orow, int rows, int phase, int &iters, int max_iter,
                          T eps_p, T eps_d) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int r0, r1;
+  own_rows(rows, r0, r1);
+  const int per = (rows + nw - 1) / nw;
+  const bool obj_warp = orow >= r0 && orow < r1;
   int degenerate_run = 0;
   bool bland = false;
+  if (w == 0) {            // Step 1 of the first pivot
+    T v;
+    int key;
+    step1_warp(S, orow, false, eps_d, -1, 0, v, key);
+    if (lane == 0) S.sel[0] = key;
+  }
+  __syncthreads();
   for (;;) {
-    // Step 1: entering column.
-    T v = pos_inf<T>();
-    int key = INT_MAX;
-    const T *orow_p = S.t + size_t(orow) * S.ld;
-    for (int j = tid; j < S.nc; j += nt) {
-      const int var = S.nonb[j];
-      if (var >= S.nm) continue;
-      const T r = orow_p[j];
-      if (r < -eps_d) keep_better(v, key, bland ? T(0) : r, (var << kIdxBits) | j);
+    const int ekey = S.sel[0];
+    if (ekey == INT_MAX) {
+      __syncthreads();       // the last pivot row copy is visible to every warp
+      return LPB_OPTIMAL;
     }
-    block_argmin(v, key, S.redv, S.redk);
-    if (key == INT_MAX) return LPB_OPTIMAL;
-    const int e = key & kIdxMask;
-    // Step 2: leaving row by the minimum ratio.
-    v = pos_inf<T>();
-    key = INT_MAX;
-    for (int i = tid; i < S.m; i += nt) {
-      const int bv = S.basic[i];
-      if (phase == 2 && bv >= S.nm) continue;
-      const T a = S.t[size_t(i) * S.ld + e];
-      if (a > eps_p) keep_better(v, key, S.t[size_t(i) * S.ld + S.nc] / a, (bv << kIdxBits) | i);
+    const int e = ekey & kIdxMask;
+    // Step 2 on this warp's rows, and the reciprocal of its best pivot.
+    {
+      T v = pos_inf<T>();
+      int key = INT_MAX;
+      const int hi = min(r1, S.m);
+      if constexpr (sizeof(T) == 8) {
+        // FP64 division runs on the slow FP64 pipe, so the ratios are first
+        // formed in FP32 (relative error below 3e-7) and, after one more
+        // barrier, only rows within 1e-5 of the smallest FP32 ratio of the
+        // whole tableau get the exact FP64 quotient.  The exact minimum and
+        // every exact tie are always among them, so the choice is the one the
+        // FP64 quotients of all rows would give; only the warps holding such
+        // rows divide, and they alone form the reciprocal of their pivot.
+        float m32 = __int_as_float(0x7f800000);
+        for (int i = r0 + lane; i < hi; i += 32) {
+          const int bv = S.basic[i];
+          if (phase == 2 && bv >= S.nm) continue;
+          const T *ri = S.row(i);
+          const T a = ri[e];
+          if (a > eps_p) m32 = fminf(m32, __fdiv_rn(d2f_rn(ri[S.nc]), d2f_rn(a)));
+        }
+        m32 = ord2f(__reduce_min_sync(kFull, f2ord(m32)));
+        if (lane == 0) S.redf[w] = m32;
+        __syncthreads();
+        float g32 = lane < nw ? S.redf[lane] : __int_as_float(0x7f800000);
+        g32 = ord2f(__reduce_min_sync(kFull, f2ord(g32)));
+        const float cut = g32 + 1e-5f * fabsf(g32);
+        if (m32 <= cut) {
+          for (int i = r0 + lane; i < hi; i += 32) {
+            const int bv = S.basic[i];
+            if (phase == 2 && bv >= S.nm) continue;
+            const T *ri = S.row(i);
+            const T a = ri[e];
+            if (a > eps_p && !(__fdiv_rn(d2f_rn(ri[S.nc]), d2f_rn(a)) > cut))
+              keep_better(v, key, ri[S.nc] / a, (bv << kIdxBits) | i);
+          }
+        }
+      } else {
+        for (int i = r0 + lane; i < hi; i += 32) {
+          const int bv = S.basic[i];
+          if (phase == 2 && bv >= S.nm) continue;
+          const T *ri = S.row(i);
+          const T a = ri[e];
+          if (a > eps_p) keep_better(v, key, ri[S.nc] / a, (bv << kIdxBits) | i);
+        }
+      }
+      warp_argmin(v, key);
+      if (lane == 0) {
+        S.redv[32 + w] = v;
+        S.redk[32 + w] = key;
+        if (key != INT_MAX) S.rcp[w] = T(1) / S.at(key & kIdxMask, e);
+      }
     }
-    block_argmin(v, key, S.redv + 32, S.redk + 32);
-    if (key == INT_MAX) return phase == 2 ? LPB_UNBOUNDED : LPB_NUMERIC;
+    __syncthreads();
+    T theta = pos_inf<T>();
+    int lkey = INT_MAX;
+    if (lane < nw) { theta = S.redv[32 + lane]; lkey = S.redk[32 + lane]; }
+    warp_argmin(theta, lkey);
+    if (lkey == INT_MAX) return phase == 2 ? LPB_UNBOUNDED : LPB_NUMERIC;
     if (iters >= max_iter) return LPB_ITER_LIMIT;
-    const int l = key & kIdxMask;
-    pivot(S, rows, l, e);
+    const int l = lkey & kIdxMask, leave = lkey >> kIdxBits;
+    const T rp = S.rcp[l / per];
+    if (threadIdx.x == 0) {
+      S.basic[l] = S.nonb[e];
+      S.nonb[e] = leave;
+    }
+    update_any(S, rows, l, e, rp);
     ++iters;
-    if (v <= eps_p) {
+    if (theta <= eps_p) {
       if (++degenerate_run >= S.m + S.n) bland = true;
     } else {
       degenerate_run = 0;
       bland = false;
     }
+    if (obj_warp) {        // Step 1 of the next pivot on the updated objective row
+      __syncwarp();
+      T v;
+      int key;
+      step1_warp(S, orow, bland, eps_d, e, leave, v, key);
+      if (lane == 0) S.sel[0] = key;
+    }
+    __syncthreads();
+    pivot_finish(S, rows, l);
   }
 }
 
 // Largest |t_ij| over enterable columns of row i (ties: lowest column); -1 if
 // none exceeds `eps`.
 template <typename T>
-__device__ int row_argmax_abs(Tab<T> &S, int i, T eps, int set) {
+__device__ __forceinline__ int row_argmax_abs(const Tab<T> &S_, int i, T eps, int set) {
+  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
   T v = pos_inf<T>();
   int key = INT_MAX;
   for (int j = threadIdx.x; j < S.nc; j += blockDim.x) {
     if (S.nonb[j] >= S.nm) continue;
-    const T a = fabs(S.t[size_t(i) * S.ld + j]);
+    const T a = fabs(S.at(i, j));
     if (a > eps) keep_better(v, key, -a, j);
   }
   block_argmin(v, key, S.redv + 32 * set, S.redk + 32 * set);
@@ -214,7 +402,8 @@ __device__ int row_argmax_abs(Tab<T> &S, int i, T eps, int set) {
 
 // Column currently holding non-basic variable `var`; -1 if it is basic.
 template <typename T>
-__device__ int column_of(Tab<T> &S, int var, int set) {
+__device__ __forceinline__ int column_of(const Tab<T> &S_, int var, int set) {
+  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
   int key = INT_MAX;
   T v = pos_inf<T>();
   for (int j = threadIdx.x; j < S.nc; j += blockDim.x)
@@ -226,7 +415,7 @@ __device__ int column_of(Tab<T> &S, int var, int set) {
 // Warp 0 writes the indices i < cnt with pred(i) into out[] in increasing
 // order and returns the count (to every thread, after a barrier).
 template <typename Pred>
-__device__ int compact(int cnt, int *out, int *s_cnt, Pred pred) {
+__device__ __forceinline__ int compact(int cnt, int *out, int *s_cnt, Pred pred) {
   if ((threadIdx.x >> 5) == 0) {
     const int lane = threadIdx.x & 31;
     int base = 0;
@@ -247,12 +436,18 @@ __device__ int compact(int cnt, int *out, int *s_cnt, Pred pred) {
 // an artificial each and the Phase-I row when some b_i < 0).  Returns false
 // if the data holds NaN or Inf.
 template <typename T>
-__device__ bool build_tableau(Tab<T> &S, const BatchDev &B, int lp, int64_t aoff, int64_t boff,
+__device__ __forceinline__ bool build_tableau(const Tab<T> &S_, const BatchDev &B_, int lp, int64_t aoff, int64_t boff,
                               int64_t coff) {
+  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
+  const BatchDev B = B_;
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
   const int m = S.m, n = S.n, ld = S.ld, nc = S.nc;
   const int rows = m + (S.k ? 2 : 1);
-  for (size_t idx = tid; idx < size_t(rows) * ld; idx += nt) S.t[idx] = T(0);
+  {
+    const int rsm = min(rows, S.rs);
+    for (size_t idx = tid; idx < size_t(rsm) * ld; idx += nt) S.ts[idx] = T(0);
+    for (size_t idx = tid; idx < size_t(rows - rsm) * ld; idx += nt) S.tg[idx] = T(0);
+  }
   for (int j = tid; j < n; j += nt) S.nonb[j] = j;
   if (tid == 0) S.nonb[nc] = -1;
   __syncthreads();
@@ -267,7 +462,7 @@ __device__ bool build_tableau(Tab<T> &S, const BatchDev &B, int lp, int64_t aoff
         if (neg) {
           const int col = n + base + __popc(mask & ((1u << lane) - 1u));
           S.nonb[col] = n + i;
-          S.t[size_t(i) * ld + col] = T(-1);
+          S.at(i, col) = T(-1);
         }
       }
       base += __popc(mask);
@@ -293,7 +488,7 @@ __device__ bool build_tableau(Tab<T> &S, const BatchDev &B, int lp, int64_t aoff
         const int i = i0 + u * nw;
         if (i >= m) continue;
         const T s = S.basic[i] >= n + m ? T(-1) : T(1);
-        T *row = S.t + size_t(i) * ld;
+        T *row = S.row(i);
 #pragma unroll
         for (int w = 0; w < kU; ++w) {
           const int j = j0 + 32 * w;
@@ -308,20 +503,20 @@ __device__ bool build_tableau(Tab<T> &S, const BatchDev &B, int lp, int64_t aoff
   for (int i = tid; i < m; i += nt) {
     const T bi = ld_as<T>(B.b, boff + i, B.dtype);
     bad |= !isfinite(bi);
-    S.t[size_t(i) * ld + nc] = S.basic[i] >= n + m ? -bi : bi;
+    S.at(i, nc) = S.basic[i] >= n + m ? -bi : bi;
   }
   for (int j = tid; j < n; j += nt) {
     const T cj = ld_as<T>(B.c, coff + j, B.dtype);
     bad |= !isfinite(cj);
-    S.t[size_t(m) * ld + j] = -cj;
+    S.at(m, j) = -cj;
   }
   bad = __syncthreads_or(bad);
   if (S.k) {   // Phase-I row: w = -(sum of artificials) in the non-basic variables
     for (int j = tid; j <= nc; j += nt) {
       T s = T(0);
       for (int i = 0; i < m; ++i)
-        if (S.basic[i] >= n + m) s += S.t[size_t(i) * ld + j];
-      S.t[size_t(m + 1) * ld + j] = -s;
+        if (S.basic[i] >= n + m) s += S.at(i, j);
+      S.at(m + 1, j) = -s;
     }
     __syncthreads();
   }
@@ -332,7 +527,8 @@ __device__ bool build_tableau(Tab<T> &S, const BatchDev &B, int lp, int64_t aoff
 // into the basis.  Returns false when a pivot would be (near) singular or the
 // resulting basic solution is infeasible; the caller then starts cold.
 template <typename T>
-__device__ bool warm_start(Tab<T> &S, const int32_t *warm, int &iters, T eps_p) {
+__device__ __forceinline__ bool warm_start(const Tab<T> &S_, const int32_t *warm, int &iters, T eps_p) {
+  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
   const int tid = threadIdx.x, nt = blockDim.x;
   const int m = S.m, nm = S.nm;
   __shared__ int s_ok;
@@ -358,7 +554,7 @@ __device__ bool warm_start(Tab<T> &S, const int32_t *warm, int &iters, T eps_p) 
     for (int i = tid; i < m; i += nt) {
       const int bv = S.basic[i];
       if (bv < nm && S.ins[bv]) continue;
-      const T a = fabs(S.t[size_t(i) * S.ld + e]);
+      const T a = fabs(S.at(i, e));
       if (a > T(1e-9)) keep_better(bvv, key, -a, i);
     }
     block_argmin(bvv, key, S.redv + 32, S.redk + 32);
@@ -377,7 +573,8 @@ __device__ bool warm_start(Tab<T> &S, const int32_t *warm, int &iters, T eps_p) 
 // basic value is >= -eps_p; false if a row has no entering column or the cap
 // is reached (the caller then starts cold).
 template <typename T>
-__device__ bool dual_cleanup(Tab<T> &S, int rows, int &iters, int max_iter, T eps_p) {
+__device__ __forceinline__ bool dual_cleanup(const Tab<T> &S_, int rows, int &iters, int max_iter, T eps_p) {
+  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
   const int tid = threadIdx.x, nt = blockDim.x;
   for (;;) {
     __syncthreads();
@@ -386,7 +583,7 @@ __device__ bool dual_cleanup(Tab<T> &S, int rows, int &iters, int max_iter, T ep
     for (int i = tid; i < S.m; i += nt) {
       const int bv = S.basic[i];
       if (bv >= S.nm) continue;
-      const T rhs = S.t[size_t(i) * S.ld + S.nc];
+      const T rhs = S.at(i, S.nc);
       if (rhs < -eps_p) keep_better(v, key, rhs, (bv << kIdxBits) | i);
     }
     block_argmin(v, key, S.redv, S.redk);
@@ -397,8 +594,8 @@ __device__ bool dual_cleanup(Tab<T> &S, int rows, int &iters, int max_iter, T ep
     for (int j = tid; j < S.nc; j += nt) {
       const int var = S.nonb[j];
       if (var >= S.nm) continue;
-      const T a = S.t[size_t(l) * S.ld + j];
-      if (a < -eps_p) keep_better(v, key, S.t[size_t(S.m) * S.ld + j] / -a, (var << kIdxBits) | j);
+      const T a = S.at(l, j);
+      if (a < -eps_p) keep_better(v, key, S.at(S.m, j) / -a, (var << kIdxBits) | j);
     }
     block_argmin(v, key, S.redv + 32, S.redk + 32);
     if (key == INT_MAX || iters >= max_iter) return false;
@@ -413,8 +610,10 @@ __device__ __forceinline__ int32_t *basis_at(const TableauParams &P, int lp, int
 }
 
 template <typename T>
-__device__ void write_from_tableau(Tab<T> &S, const ResultDev &R, int32_t *basis, int lp,
+__device__ __forceinline__ void write_from_tableau(const Tab<T> &S_, const ResultDev &R_, int32_t *basis, int lp,
                                    int64_t boff, int64_t coff, int status, int iters) {
+  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
+  const ResultDev R = R_;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int m = S.m, n = S.n;
   for (int j = tid; j < n; j += nt) R.x[coff + j] = 0.0;
@@ -423,12 +622,12 @@ __device__ void write_from_tableau(Tab<T> &S, const ResultDev &R, int32_t *basis
   if (status == LPB_OPTIMAL) {
     for (int i = tid; i < m; i += nt) {
       const int v = S.basic[i];
-      if (v < n) R.x[coff + v] = double(S.t[size_t(i) * S.ld + S.nc]);
+      if (v < n) R.x[coff + v] = double(S.at(i, S.nc));
     }
     if (R.y)
       for (int j = tid; j < S.nc; j += nt) {
         const int v = S.nonb[j];
-        if (v >= n && v < n + m) R.y[boff + (v - n)] = double(S.t[size_t(m) * S.ld + j]);
+        if (v >= n && v < n + m) R.y[boff + (v - n)] = double(S.at(m, j));
       }
   }
   if (basis)
@@ -436,7 +635,7 @@ __device__ void write_from_tableau(Tab<T> &S, const ResultDev &R, int32_t *basis
   if (tid == 0) {
     R.status[lp] = status;
     if (R.iters) R.iters[lp] = iters;
-    R.obj[lp] = status == LPB_OPTIMAL ? double(S.t[size_t(m) * S.ld + S.nc])
+    R.obj[lp] = status == LPB_OPTIMAL ? double(S.at(m, S.nc))
               : status == LPB_INFEASIBLE ? -INFINITY
               : status == LPB_UNBOUNDED ? INFINITY : NAN;
   }
@@ -444,23 +643,30 @@ __device__ void write_from_tableau(Tab<T> &S, const ResultDev &R, int32_t *basis
 
 // FP64 refinement and verification of an FP32-optimal basis.  Returns true and
 // writes the outputs when the refined pair (x, y) passes the checks.
-__device__ bool refine_and_verify(Tab<float> &S, const BatchDev &B, const ResultDev &R,
-                                  int32_t *basis, const Layout &L, unsigned char *smem, int lp,
-                                  int64_t aoff,
-                                  int64_t boff, int64_t coff, int iters, double tol, double bmax,
-                                  double cmax) {
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
-  const int m = S.m, n = S.n, ld = S.ld, nc = S.nc;
-  double *xb = reinterpret_cast<double *>(smem + L.xb);
-  double *rr = reinterpret_cast<double *>(smem + L.rr);
-  double *yv = reinterpret_cast<double *>(smem + L.yv);
-  double *rho = reinterpret_cast<double *>(smem + L.rho);
+__device__ __forceinline__ bool refine_and_verify(const Tab<float> &S_, const BatchDev &B_, const ResultDev &R_,
+                                                  int32_t *basis, const Layout &L, unsigned char *smem, int lp,
+                                                  int64_t aoff, int64_t boff, int64_t coff, int iters, double tol,
+                                                  double bmax, double cmax) {
+  const Tab<float> S = S_;   // a register copy: stores through tableau pointers cannot alias it
+  const BatchDev B = B_;
+  const ResultDev R = R_;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int m = S.m, n = S.n, nc = S.nc;
+  double *xb = reinterpret_cast<double *>(smem + L.xb);    // x_B by row
+  double *rr = reinterpret_cast<double *>(smem + L.rr);    // primal residual b - [A I]_B x_B by row
+  double *yv = reinterpret_cast<double *>(smem + L.yv);    // y by slack
+  double *rho = reinterpret_cast<double *>(smem + L.rho);  // dual residual by row of a basic structural
+  double *dj = reinterpret_cast<double *>(smem + L.dj);    // reduced costs A^T y - c by column
   int *sb = reinterpret_cast<int *>(smem + L.sb);   // rows whose basic variable is structural
   int *ns = reinterpret_cast<int *>(smem + L.ns);   // columns holding a non-basic slack
   int *sp = reinterpret_cast<int *>(smem + L.sp);   // row of basic slack k, or -1
+  int *jq = reinterpret_cast<int *>(smem + L.jq);   // column of A of the q-th basic structural
+  int *kq = reinterpret_cast<int *>(smem + L.kq);   // slack (row of A) of the p-th non-basic slack
   __shared__ int s_cnt0, s_cnt1;
   __shared__ double s_red[2][32];
+  __shared__ unsigned long long s_nrm[2];
   const int dt = B.dtype;
+  const double tp = tol * (1.0 + bmax), td = tol * (1.0 + cmax);
 
   const int nsb = compact(m, sb, &s_cnt0, [&](int i) { return S.basic[i] < n; });
   const int nns = compact(nc, ns, &s_cnt1, [&](int j) { const int v = S.nonb[j]; return v >= n && v < n + m; });
@@ -468,101 +674,126 @@ __device__ bool refine_and_verify(Tab<float> &S, const BatchDev &B, const Result
   __syncthreads();
   for (int i = tid; i < m; i += nt) {
     const int v = S.basic[i];
-    xb[i] = double(S.t[size_t(i) * ld + nc]);
+    xb[i] = double(S.at(i, nc));
     if (v >= n && v < n + m) sp[v - n] = i;
   }
-  for (int q = tid; q < nns; q += nt) yv[S.nonb[ns[q]] - n] = double(S.t[size_t(m) * ld + ns[q]]);
-  __syncthreads();
-  // Primal residual r = b - [A I]_B x_B in FP64.
-  for (int i = tid; i < m; i += nt) {
-    double r = ld_in(B.b, boff + i, dt);
-    const int64_t ar = aoff + int64_t(i) * n;
-#pragma unroll 4
-    for (int q = 0; q < nsb; ++q) {
-      const int t = sb[q];
-      r = fma(-ld_in(B.A, ar + S.basic[t], dt), xb[t], r);
-    }
-    if (sp[i] >= 0) r -= xb[sp[i]];
-    rr[i] = r;
-  }
-  // Dual residual rho_t = c_B(t) - (B^T y)_t for structural basic rows (slack rows: 0).
-  for (int q = tid; q < nsb; q += nt) {
-    const int t = sb[q], j = S.basic[t];
-    double r = ld_in(B.c, coff + j, dt);
-#pragma unroll 4
-    for (int p = 0; p < nns; ++p) {
-      const int kk = S.nonb[ns[p]] - n;
-      r = fma(-ld_in(B.A, aoff + int64_t(kk) * n + j, dt), yv[kk], r);
-    }
-    rho[t] = r;
-  }
-  __syncthreads();
-  // Corrections with the FP32 basis inverse: its column for slack k is the
-  // tableau column of k when k is non-basic, else the unit vector of k's row.
-  for (int t = tid; t < m; t += nt) {
-    float d = 0.f;
-    const float *row = S.t + size_t(t) * ld;
-    for (int p = 0; p < nns; ++p) {
-      const int col = ns[p];
-      d = fmaf(float(rr[S.nonb[col] - n]), row[col], d);
-    }
-    const int v = S.basic[t];
-    double dx = double(d);
-    if (v >= n && v < n + m) dx += rr[v - n];
-    xb[t] += dx;
-  }
+  for (int q = tid; q < nsb; q += nt) jq[q] = S.basic[sb[q]];
   for (int p = tid; p < nns; p += nt) {
-    const int col = ns[p];
-    float d = 0.f;
-    for (int q = 0; q < nsb; ++q) {
-      const int t = sb[q];
-      d = fmaf(float(rho[t]), S.t[size_t(t) * ld + col], d);
-    }
-    yv[S.nonb[col] - n] += double(d);
+    const int k = S.nonb[ns[p]] - n;
+    kq[p] = k;
+    yv[k] = double(S.at(m, ns[p]));
   }
-  __syncthreads();
+  // Iterative refinement (at most kSteps corrections) of x_B = B^{-1} b and
+  // y = B^{-T} c_B with FP64 residuals and the FP32 basis inverse held in the
+  // tableau, until the residuals are 1000 times below the certificate's
+  // tolerance.  The residuals of the last pass are the certificate's slacks
+  // and reduced costs.
+  constexpr int kSteps = 3;
+  for (int step = 0;; ++step) {
+    if (tid == 0) { s_nrm[0] = 0ull; s_nrm[1] = 0ull; }
+    __syncthreads();
+    // Primal residual r = b - A_S x_S - x_slack.  Each row's sum over the
+    // basic structurals is split over a group of G lanes (G the largest power
+    // of two with G m <= threads, at most 32), combined by butterflies in a
+    // fixed order.
+    double np = 0.0, nd = 0.0;
+    {
+      int G = 1;
+      while (G < 32 && 2 * G * m <= nt) G *= 2;
+      const int g = lane & (G - 1), rows_per_pass = nt / G;
+      for (int i0 = 0; i0 < m; i0 += rows_per_pass) {
+        const int i = i0 + tid / G;
+        const bool live = i < m;
+        const int64_t ar = aoff + int64_t(live ? i : 0) * n;
+        double s0 = 0.0, s1 = 0.0;
+        int q = g;
+        for (; q + G < nsb; q += 2 * G) {
+          s0 = fma(ld_in(B.A, ar + jq[q], dt), xb[sb[q]], s0);
+          s1 = fma(ld_in(B.A, ar + jq[q + G], dt), xb[sb[q + G]], s1);
+        }
+        if (q < nsb) s0 = fma(ld_in(B.A, ar + jq[q], dt), xb[sb[q]], s0);
+        double sum = s0 + s1;
+        for (int off = 1; off < G; off *= 2) sum += __shfl_xor_sync(kFull, sum, off);
+        if (live && g == 0) {
+          double r = ld_in(B.b, boff + i, dt) - sum;
+          if (sp[i] >= 0) r -= xb[sp[i]];
+          rr[i] = r;
+          np = fmax(np, fabs(r));
+        }
+      }
+    }
+    // Reduced costs d_j = A_j^T y - c_j of every column, one thread per column.
+    for (int j = tid; j < n; j += nt) {
+      double d = -ld_in(B.c, coff + j, dt);
+#pragma unroll 8
+      for (int p = 0; p < nns; ++p) {
+        const int k = kq[p];
+        d = fma(ld_in(B.A, aoff + int64_t(k) * n + j, dt), yv[k], d);
+      }
+      dj[j] = d;
+    }
+    if (np > 0.0) atomicMax(&s_nrm[0], static_cast<unsigned long long>(__double_as_longlong(np)));
+    __syncthreads();
+    for (int q = tid; q < nsb; q += nt) {      // dual residual c_B - B^T y on the basic structurals
+      const double r = -dj[jq[q]];
+      rho[sb[q]] = r;
+      nd = fmax(nd, fabs(r));
+    }
+    if (nd > 0.0) atomicMax(&s_nrm[1], static_cast<unsigned long long>(__double_as_longlong(nd)));
+    __syncthreads();
+    const double rp_ = __longlong_as_double(static_cast<long long>(s_nrm[0]));
+    const double rd_ = __longlong_as_double(static_cast<long long>(s_nrm[1]));
+    if (step == kSteps || (rp_ <= 1e-3 * tp && rd_ <= 1e-3 * td)) break;   // 1000x below the certificate's bar
+    // Corrections with the FP32 basis inverse: its column for slack k is the
+    // tableau column of k when k is non-basic, else the unit vector of k's row.
+    for (int t = tid; t < m; t += nt) {
+      float d = 0.f;
+      const float *row = S.row(t);
+      for (int p = 0; p < nns; ++p) d = fmaf(float(rr[kq[p]]), row[ns[p]], d);
+      const int v = S.basic[t];
+      double dx = double(d);
+      if (v >= n && v < n + m) dx += rr[v - n];
+      xb[t] += dx;
+    }
+    for (int p = tid; p < nns; p += nt) {
+      const int col = ns[p];
+      float d = 0.f;
+      for (int q = 0; q < nsb; ++q) {
+        const int t = sb[q];
+        d = fmaf(float(rho[t]), S.at(t, col), d);
+      }
+      yv[kq[p]] += double(d);
+    }
+    __syncthreads();
+  }
   // FP64 KKT certificate of the pair that is written out (x: the structural
   // part of x_B; y: the slack duals): x >= 0, A x <= b, y >= 0, A^T y >= c and
-  // c^T x = b^T y, each to tol scaled by the data.
+  // c^T x = b^T y, each to tol scaled by the data.  The slack of row i is its
+  // residual plus its basic slack's value.
   double cx = 0.0, by = 0.0;
   int bad = 0;
-  const double tp = tol * (1.0 + bmax), td = tol * (1.0 + cmax);
   for (int q = tid; q < nsb; q += nt) {
     bad |= !(xb[sb[q]] >= -tp);
-    cx = fma(ld_in(B.c, coff + S.basic[sb[q]], dt), xb[sb[q]], cx);
+    cx = fma(ld_in(B.c, coff + jq[q], dt), xb[sb[q]], cx);
   }
   for (int p = tid; p < nns; p += nt) {
-    const int kk = S.nonb[ns[p]] - n;
-    by = fma(ld_in(B.b, boff + kk, dt), yv[kk], by);
-    bad |= !(yv[kk] >= -td);
+    const int k = kq[p];
+    by = fma(ld_in(B.b, boff + k, dt), yv[k], by);
+    bad |= !(yv[k] >= -td);
   }
-  for (int i = tid; i < m; i += nt) {     // slack b_i - A_i x of every row
-    double s = ld_in(B.b, boff + i, dt);
-    const int64_t ar = aoff + int64_t(i) * n;
-#pragma unroll 4
-    for (int q = 0; q < nsb; ++q) s = fma(-ld_in(B.A, ar + S.basic[sb[q]], dt), xb[sb[q]], s);
-    bad |= !(s >= -tp);
-  }
-  for (int j = tid; j < n; j += nt) {     // reduced cost A_j^T y - c_j of every column
-    double d = -ld_in(B.c, coff + j, dt);
-#pragma unroll 4
-    for (int p = 0; p < nns; ++p) {
-      const int kk = S.nonb[ns[p]] - n;
-      d = fma(ld_in(B.A, aoff + int64_t(kk) * n + j, dt), yv[kk], d);
-    }
-    bad |= !(d >= -td);
-  }
+  for (int i = tid; i < m; i += nt) bad |= !(rr[i] + (sp[i] >= 0 ? xb[sp[i]] : 0.0) >= -tp);
+  for (int j = tid; j < n; j += nt) bad |= !(dj[j] >= -td);
   cx = warp_sum(cx);
   by = warp_sum(by);
   if (lane == 0) { s_red[0][wid] = cx; s_red[1][wid] = by; }
   bad = __syncthreads_or(bad);
   cx = 0.0; by = 0.0;
-  for (int w = 0; w < (nt >> 5); ++w) { cx += s_red[0][w]; by += s_red[1][w]; }
+  for (int w = 0; w < nw; ++w) { cx += s_red[0][w]; by += s_red[1][w]; }
   bad |= !(fabs(cx - by) <= tol * (1.0 + fabs(cx)));
   if (bad) return false;
   for (int j = tid; j < n; j += nt) R.x[coff + j] = 0.0;
   __syncthreads();
-  for (int q = tid; q < nsb; q += nt) R.x[coff + S.basic[sb[q]]] = xb[sb[q]];
+  for (int q = tid; q < nsb; q += nt) R.x[coff + jq[q]] = xb[sb[q]];
   if (R.y) for (int k = tid; k < m; k += nt) R.y[boff + k] = yv[k];
   if (basis) for (int i = tid; i < m; i += nt) basis[i] = S.basic[i];
   if (tid == 0) {
@@ -573,23 +804,26 @@ __device__ bool refine_and_verify(Tab<float> &S, const BatchDev &B, const Result
   return true;
 }
 
-template <typename T, bool kGmem>
+template <typename T>
 __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, nt = blockDim.x;
   const bool refine = (P.mode == MODE_FP32_REFINE) && sizeof(T) == 4;
-  const Layout L = make_layout(int(sizeof(T)), kGmem, P.B.max_m, P.B.max_n, P.kcap, refine);
+  const Layout L = make_layout(int(sizeof(T)), P.tab_smem, P.B.max_m, P.B.max_n, P.kcap, refine);
   Tab<T> S;
-  S.t = kGmem ? reinterpret_cast<T *>(static_cast<unsigned char *>(P.slots) + size_t(blockIdx.x) * P.slot_bytes)
-              : reinterpret_cast<T *>(smem + L.tab);
+  S.ts = reinterpret_cast<T *>(smem + L.tab);
+  S.tg = P.slot_bytes ? reinterpret_cast<T *>(static_cast<unsigned char *>(P.slots) + size_t(blockIdx.x) * P.slot_bytes)
+                      : nullptr;
   S.colb = reinterpret_cast<T *>(smem + L.colb);
   S.rowb = reinterpret_cast<T *>(smem + L.rowb);
   S.basic = reinterpret_cast<int *>(smem + L.basic);
   S.nonb = reinterpret_cast<int *>(smem + L.nonb);
   S.redv = reinterpret_cast<T *>(smem + L.redv);
   S.redk = reinterpret_cast<int *>(smem + L.redk);
+  S.rcp = reinterpret_cast<T *>(smem + L.rcp);
+  S.redf = reinterpret_cast<float *>(smem + L.redf);
+  S.sel = reinterpret_cast<int *>(smem + L.sel);
   S.ins = smem + L.ins;
-  S.gmem = kGmem;
   __shared__ int s_item, s_k;
   __shared__ unsigned long long s_bmax, s_cmax;
   const T eps_p = T(P.eps_p), eps_d = T(P.eps_d);
@@ -628,7 +862,23 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
     if (bm == bm) atomicMax(&s_bmax, static_cast<unsigned long long>(__double_as_longlong(bm)));
     if (cm == cm) atomicMax(&s_cmax, static_cast<unsigned long long>(__double_as_longlong(cm)));
     __syncthreads();
-    S.m = m; S.n = n; S.k = s_k; S.nc = n + S.k; S.ld = tab_ld(n, S.k); S.nm = n + m;
+    S.m = m; S.n = n; S.k = s_k; S.nc = n + S.k; S.ld = tab_ld(n, S.k, int(sizeof(T))); S.nm = n + m;
+    {
+      // Leading rows in shared memory as far as they fit, the rest in the slot.
+      const int rows = m + (S.k ? 2 : 1);
+      const size_t row_bytes = size_t(S.ld) * sizeof(T);
+      S.rs = int(min(size_t(rows), P.tab_smem / row_bytes));
+      if (size_t(rows - S.rs) * row_bytes > P.slot_bytes && S.k <= P.kcap) {
+        if (tid == 0) {
+          atomicOr(P.err, ERR_SLOT_OVERFLOW);
+          P.R.status[lp] = LPB_NUMERIC;
+          if (P.R.iters) P.R.iters[lp] = 0;
+          P.R.obj[lp] = NAN;
+        }
+        __syncthreads();
+        continue;
+      }
+    }
     const double bmax = __longlong_as_double(static_cast<long long>(s_bmax));
     const double cmax = __longlong_as_double(static_cast<long long>(s_cmax));
     if (S.k > P.kcap) {        // needs more artificial columns than this launch holds
@@ -660,12 +910,12 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
         // its starting value (minus the sum of the negated right-hand sides), so
         // its infeasibility test is relative to that; the FP64 certificate and
         // re-solve settle the LPs it lets through.
-        const double w0 = -double(S.t[size_t(m + 1) * S.ld + S.nc]);
+        const double w0 = -double(S.at(m + 1, S.nc));
         const double ftol = sizeof(T) == 4 ? fmax(P.feas_tol * (1.0 + bmax), 1e-5 * (1.0 + w0))
                                            : P.feas_tol * (1.0 + bmax);
         status = run_phase(S, m + 1, m + 2, 1, iters, max_iter, eps_p, eps_d);
         if (status == LPB_OPTIMAL) {
-          const double w = double(S.t[size_t(m + 1) * S.ld + S.nc]);
+          const double w = double(S.at(m + 1, S.nc));
           if (-w > ftol) {
             status = LPB_INFEASIBLE;
           } else {             // drive zero-level artificials out of the basis
@@ -708,50 +958,32 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
 
 }  // namespace
 
-size_t tableau_smem_bytes(int eb, bool gmem, int max_m, int max_n, int kcap, int threads, bool refine) {
-  (void)threads;
-  return make_layout(eb, gmem, max_m, max_n, kcap, refine).total;
+size_t tableau_fixed_bytes(int eb, int max_m, int max_n, int kcap, bool refine) {
+  return make_layout(eb, 0, max_m, max_n, kcap, refine).total;
 }
 
-size_t tableau_slot_bytes(int eb, int max_m, int max_n, int kcap) {
-  return align16(size_t(max_m + 2) * size_t(tab_ld(max_n, kcap)) * size_t(eb));
-}
+size_t tableau_row_bytes(int eb, int max_n, int kcap) { return size_t(tab_ld(max_n, kcap, eb)) * size_t(eb); }
 
-template <typename T, bool G>
+template <typename T>
 static cudaError_t prep(size_t smem) {
-  return cudaFuncSetAttribute(tableau_kernel<T, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              int(smem));
+  return cudaFuncSetAttribute(tableau_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
 }
 
-cudaError_t tableau_max_ctas_per_sm(int eb, bool gmem, int threads, size_t smem, int *ctas) {
-  cudaError_t e;
+cudaError_t tableau_max_ctas_per_sm(int eb, int threads, size_t smem, int *ctas) {
   if (eb == 8) {
-    e = gmem ? prep<double, true>(smem) : prep<double, false>(smem);
-    if (e != cudaSuccess) return e;
-    return gmem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, tableau_kernel<double, true>, threads, smem)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, tableau_kernel<double, false>, threads, smem);
+    const cudaError_t e = prep<double>(smem);
+    return e != cudaSuccess ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, tableau_kernel<double>, threads, smem);
   }
-  e = gmem ? prep<float, true>(smem) : prep<float, false>(smem);
-  if (e != cudaSuccess) return e;
-  return gmem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, tableau_kernel<float, true>, threads, smem)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, tableau_kernel<float, false>, threads, smem);
+  const cudaError_t e = prep<float>(smem);
+  return e != cudaSuccess ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, tableau_kernel<float>, threads, smem);
 }
 
-cudaError_t launch_tableau(const TableauParams &p, bool fp64, bool gmem, int grid, int threads,
-                           size_t smem, cudaStream_t s) {
+cudaError_t launch_tableau(const TableauParams &p, bool fp64, int grid, int threads, size_t smem, cudaStream_t s) {
   if (threads < 32 || threads > kMaxThreads || (threads & 31) || grid < 1) return cudaErrorInvalidValue;
-  cudaError_t e;
-  if (fp64) {
-    e = gmem ? prep<double, true>(smem) : prep<double, false>(smem);
-    if (e != cudaSuccess) return e;
-    if (gmem) tableau_kernel<double, true><<<grid, threads, smem, s>>>(p);
-    else tableau_kernel<double, false><<<grid, threads, smem, s>>>(p);
-  } else {
-    e = gmem ? prep<float, true>(smem) : prep<float, false>(smem);
-    if (e != cudaSuccess) return e;
-    if (gmem) tableau_kernel<float, true><<<grid, threads, smem, s>>>(p);
-    else tableau_kernel<float, false><<<grid, threads, smem, s>>>(p);
-  }
+  const cudaError_t e = fp64 ? prep<double>(smem) : prep<float>(smem);
+  if (e != cudaSuccess) return e;
+  if (fp64) tableau_kernel<double><<<grid, threads, smem, s>>>(p);
+  else tableau_kernel<float><<<grid, threads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
