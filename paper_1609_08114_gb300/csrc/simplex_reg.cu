@@ -113,7 +113,8 @@ struct RegShared {
   static constexpr int ROWS = 32 * R, COLS = W * C;
   float colbuf[2][W][ROWS];                  // each warp's candidate column, by pivot parity
   WarpChoice choice[2][W];                   // by pivot parity
-  double bin[ROWS], cin[COLS];               // the LP's b and c as given (FP64 or FP32)
+  alignas(16) double bin[ROWS];              // the LP's b and c as given (FP64 or FP32)
+  alignas(16) double cin[COLS];
   float rhs[ROWS];
   int basic[ROWS];
   int nonb[COLS];
@@ -156,6 +157,20 @@ __device__ __forceinline__ float d2f_tile(double d, int &bad) {
   const bool normal = ahi >= (897u << 20);
   bad |= int(ahi >= (1151u << 20)) | int(normal & (f >= 0x7f800000u));
   return __uint_as_float((hi & 0x80000000u) | (normal ? f : 0u));
+}
+
+// FP64 -> FP32 by truncation on the integer bits (relative error below 2^-23,
+// the FP32 tableau's own precision; the refinement works with the exact A):
+// magnitudes below the smallest normal float become a signed zero.  `amax`
+// keeps the largest high word of |d| seen, so that one test afterwards
+// catches values beyond the float range, infinities and NaNs.
+__device__ __forceinline__ float d2f_trunc(double d, unsigned &amax) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(d));
+  const unsigned hi = unsigned(u >> 32), lo = unsigned(u);
+  const unsigned ahi = hi & 0x7fffffffu;
+  amax = max(amax, ahi);
+  const unsigned f = __funnelshift_l(lo, ahi - (896u << 20), 3);   // ((ahi - bias) << 3) | (lo >> 29)
+  return __uint_as_float((hi & 0x80000000u) | (ahi >= (897u << 20) ? f : 0u));
 }
 
 // Smallest power of two >= k (1 <= k <= 32).
@@ -233,7 +248,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
   const float eps_p = float(P.eps_p), eps_d = float(P.eps_d);
   const int dt = P.B.dtype;
   const int es = dt == LPB_DTYPE_F64 ? 8 : 4;
-  const int sld = a_stride(P.lim_n, es);
+  const int sld_pad = a_stride(P.lim_n, es);
   const int nitems = P.in.count ? min(*P.in.count, P.list_cap) : P.B.count;
   float T[R][C];
 
@@ -262,34 +277,62 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     // Rows of A whose global start and length are whole 16-byte units go by
     // bulk copy (the copy engine, one instruction per row); others by 4- or
     // 8-byte asynchronous copies.
-    const bool bulk = fits && ((reinterpret_cast<uintptr_t>(Ag) | uintptr_t(n) * es) & 15) == 0;
-    if (fits) {    // b and c first, then A; A's copies land while b and c are checked
-      if (dt == LPB_DTYPE_F64) {
-        const double *bg = static_cast<const double *>(P.B.b) + boff, *cg = static_cast<const double *>(P.B.c) + coff;
-        for (int i = tid; i < m; i += NT) cp_async8(sh.bin + i, bg + i);
-        for (int j = tid; j < n; j += NT) cp_async8(sh.cin + j, cg + j);
-      } else {
-        const float *bg = static_cast<const float *>(P.B.b) + boff, *cg = static_cast<const float *>(P.B.c) + coff;
-        for (int i = tid; i < m; i += NT) cp_async4(reinterpret_cast<float *>(sh.bin) + i, bg + i);
-        for (int j = tid; j < n; j += NT) cp_async4(reinterpret_cast<float *>(sh.cin) + j, cg + j);
-      }
-      if (bulk) {
-        if (wid == 0) {
-          if (lane == 0) mbar_expect_tx(&sh.abar, unsigned(m) * unsigned(n) * unsigned(es));
-          __syncwarp();
-          for (int i = lane; i < m; i += 32)
-            bulk_load(sA + size_t(i) * sld * es, Ag + size_t(i) * n * es, unsigned(n) * es, &sh.abar);
+    // A is contiguous in global memory: when its start and size are whole
+    // 16-byte units it comes in one bulk copy and keeps its row length in
+    // shared memory (one copy instruction instead of one per row, at the price
+    // of more bank conflicts in the column reads); else rows whose start and
+    // length are whole 16-byte units go by one bulk copy each into rows of a
+    // padded stride, and the rest by 4- or 8-byte asynchronous copies.
+    const bool dense = fits && ((reinterpret_cast<uintptr_t>(Ag) | uintptr_t(m) * uintptr_t(n) * es) & 15) == 0;
+    const bool bulk = fits && !dense && ((reinterpret_cast<uintptr_t>(Ag) | uintptr_t(n) * es) & 15) == 0;
+    const int sld = dense ? n : sld_pad;
+    // b and c go by bulk copy on the same barrier as A when their starts and
+    // lengths are whole 16-byte units, so that one wait covers all three.
+    const unsigned char *bgp = static_cast<const unsigned char *>(P.B.b) + boff * es;
+    const unsigned char *cgp = static_cast<const unsigned char *>(P.B.c) + coff * es;
+    const bool bulk_bc = fits && ((reinterpret_cast<uintptr_t>(bgp) | reinterpret_cast<uintptr_t>(cgp) |
+                                   uintptr_t(m) * es | uintptr_t(n) * es) & 15) == 0;
+    if (fits) {
+      if (!bulk_bc) {
+        if (dt == LPB_DTYPE_F64) {
+          const double *bg = reinterpret_cast<const double *>(bgp), *cg = reinterpret_cast<const double *>(cgp);
+          for (int i = tid; i < m; i += NT) cp_async8(sh.bin + i, bg + i);
+          for (int j = tid; j < n; j += NT) cp_async8(sh.cin + j, cg + j);
+        } else {
+          const float *bg = reinterpret_cast<const float *>(bgp), *cg = reinterpret_cast<const float *>(cgp);
+          for (int i = tid; i < m; i += NT) cp_async4(reinterpret_cast<float *>(sh.bin) + i, bg + i);
+          for (int j = tid; j < n; j += NT) cp_async4(reinterpret_cast<float *>(sh.cin) + j, cg + j);
         }
-      } else if (dt == LPB_DTYPE_F64) {
-        const double *A = reinterpret_cast<const double *>(Ag);
-        double *sa = reinterpret_cast<double *>(sA);
-        for (int i = wid; i < m; i += W)
-          for (int j = lane; j < n; j += 32) cp_async8(sa + i * sld + j, A + int64_t(i) * n + j);
-      } else {
-        const float *A = reinterpret_cast<const float *>(Ag);
-        float *sa = reinterpret_cast<float *>(sA);
-        for (int i = wid; i < m; i += W)
-          for (int j = lane; j < n; j += 32) cp_async4(sa + i * sld + j, A + int64_t(i) * n + j);
+      }
+      if (dense || bulk || bulk_bc) {
+        if (wid == 0) {
+          if (lane == 0) {
+            mbar_expect_tx(&sh.abar, (dense || bulk ? unsigned(m) * unsigned(n) * unsigned(es) : 0u) +
+                                         (bulk_bc ? unsigned(m + n) * unsigned(es) : 0u));
+            if (bulk_bc) {
+              bulk_load(sh.bin, bgp, unsigned(m) * es, &sh.abar);
+              bulk_load(sh.cin, cgp, unsigned(n) * es, &sh.abar);
+            }
+            if (dense) bulk_load(sA, Ag, unsigned(m) * unsigned(n) * es, &sh.abar);
+          }
+          __syncwarp();
+          if (bulk)
+            for (int i = lane; i < m; i += 32)
+              bulk_load(sA + size_t(i) * sld * es, Ag + size_t(i) * n * es, unsigned(n) * es, &sh.abar);
+        }
+      }
+      if (!bulk && !dense) {
+        if (dt == LPB_DTYPE_F64) {
+          const double *A = reinterpret_cast<const double *>(Ag);
+          double *sa = reinterpret_cast<double *>(sA);
+          for (int i = wid; i < m; i += W)
+            for (int j = lane; j < n; j += 32) cp_async8(sa + i * sld + j, A + int64_t(i) * n + j);
+        } else {
+          const float *A = reinterpret_cast<const float *>(Ag);
+          float *sa = reinterpret_cast<float *>(sA);
+          for (int i = wid; i < m; i += W)
+            for (int j = lane; j < n; j += 32) cp_async4(sa + i * sld + j, A + int64_t(i) * n + j);
+        }
       }
     }
     if (tid == claimer) {
@@ -299,7 +342,29 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     int neg = 0;
     if (tid == 0) { sh.bmax = 0ull; sh.cmax = 0ull; }
     cp_async_wait_all();
-    __syncthreads();
+    int timed_out = 0;
+    if (dense || bulk || bulk_bc) {
+      timed_out = !mbar_wait_bounded(&sh.abar, aphase);
+      aphase ^= 1u;
+    }
+    if (__syncthreads_or(timed_out)) {
+      // The copy engine did not deliver the data in time: hand this LP and the one
+      // claimed after it to the generic kernel, give the copies one more
+      // bounded wait, and stop this CTA.
+      if (tid == 0) {
+        atomicOr(P.err, ERR_WAIT_TIMEOUT);
+        P.R.status[lp] = STATUS_PENDING;
+        list_push(P.defer_items, P.defer_count, P.list_cap, lp, P.err);
+        mbar_wait_bounded(&sh.abar, aphase ^ 1u);
+      }
+      if (tid == claimer && next < nitems) {
+        const int lp2 = P.in.items ? P.in.items[next] : next;
+        P.R.status[lp2] = STATUS_PENDING;
+        list_push(P.defer_items, P.defer_count, P.list_cap, lp2, P.err);
+      }
+      __syncthreads();
+      break;
+    }
     if (fits) {
       // On the bits of the doubles (integer operations; FP64 ones have long
       // latency here): |v| orders like its bit pattern.  b_i < 0 or NaN and
@@ -321,29 +386,6 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       if (bm > 0ull && bm <= kInf) atomicMax(&sh.bmax, bm);
       if (cm > 0ull && cm < kInf) atomicMax(&sh.cmax, cm);
     }
-    int timed_out = 0;
-    if (bulk) {
-      timed_out = !mbar_wait_bounded(&sh.abar, aphase);
-      aphase ^= 1u;
-    }
-    if (__syncthreads_or(timed_out)) {
-      // The copy engine did not deliver A in time: hand this LP and the one
-      // claimed after it to the generic kernel, give the copies one more
-      // bounded wait, and stop this CTA.
-      if (tid == 0) {
-        atomicOr(P.err, ERR_WAIT_TIMEOUT);
-        P.R.status[lp] = STATUS_PENDING;
-        list_push(P.defer_items, P.defer_count, P.list_cap, lp, P.err);
-        mbar_wait_bounded(&sh.abar, aphase ^ 1u);
-      }
-      if (tid == claimer && next < nitems) {
-        const int lp2 = P.in.items ? P.in.items[next] : next;
-        P.R.status[lp2] = STATUS_PENDING;
-        list_push(P.defer_items, P.defer_count, P.list_cap, lp2, P.err);
-      }
-      __syncthreads();
-      break;
-    }
     neg = __syncthreads_or(neg);
     if (!fits || neg) {      // the shared-memory kernel handles it (Phase I, sizes, bad data)
       if (tid == 0) {
@@ -360,15 +402,17 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     int bad = 0;
     if (dt == LPB_DTYPE_F64) {
       const double *sa = reinterpret_cast<const double *>(sA);
+      unsigned amax = 0u;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int i = lane + 32 * r;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           const int j = wid + W * c;
-          T[r][c] = (i < m && j < n) ? d2f_tile(sa[i * sld + j], bad) : 0.f;
+          T[r][c] = (i < m && j < n) ? d2f_trunc(sa[i * sld + j], amax) : 0.f;
         }
       }
+      bad |= int(amax >= (1151u << 20));     // |a| >= 2^128, Inf or NaN
     } else {
       const float *sa = reinterpret_cast<const float *>(sA);
 #pragma unroll
