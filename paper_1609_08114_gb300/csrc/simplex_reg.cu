@@ -771,117 +771,130 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       mag = e0;
       return s0;
     };
-    // Residuals in FP64: sax = b - A x and r = sax - x_slack (rows, on the low
-    // threads); the reduced costs d = A^T y - c of every column (high
-    // threads), whose negatives on the basic structurals are the dual residual.
-    for (int i = tid; i < m; i += NT) {
-      const double ax = vin(sh.bin, i, dt) - row_dot(i);
-      const double r = sh.sp[i] >= 0 ? ax - sh.xb[sh.sp[i]] : ax;
-      sh.sax[i] = ax;
-      sh.rr[i] = r;
-      sh.rrf[i] = float(r);
-    }
-    for (int j = NT - 1 - tid; j < n; j += NT) {
-      const double d = col_dot(j) - vin(sh.cin, j, dt);
-      sh.dj[j] = d;
-      if (sh.posx[j] >= 0) sh.rhof[sh.posx[j]] = float(-d);
-    }
-    __syncthreads();
-    // Corrections with the FP32 basis inverse held in registers: its column for
-    // slack k is the tableau column of k when k is non-basic, else a unit vector.
-    {
-      constexpr int CP = pow2_at_least(C);
-      float coef[C];
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const int v = sh.nonb[wid + W * c];
-        coef[c] = (c < C - 1 || wid < W - 1) && v >= n && v < n + m ? sh.rrf[v - n] : 0.f;
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        float s = 0.f;
-#pragma unroll
-        for (int c = 0; c < C; ++c) s = fmaf(T[r][c], coef[c], s);
-        sh.part[wid][lane + 32 * r] = s;
-      }
-      float rf[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) rf[r] = sh.rhof[lane + 32 * r];
-      float dy[CP];
-#pragma unroll
-      for (int c = 0; c < CP; ++c) {
-        float s = 0.f;
-        if (c < C) {
-#pragma unroll
-          for (int r = 0; r < R; ++r) s = fmaf(T[r][c], rf[r], s);
-        }
-        dy[c] = s;
-      }
-      // Column sums across the lanes; lane l ends with column l / (32 / CP),
-      // and the first lane of each group applies it to y.
-      const float tot = reduce_scatter<CP>(dy, lane);
-      const int c = lane / (32 / CP);
-      if (lane % (32 / CP) == 0 && c < C && (c < C - 1 || wid < W - 1)) {
-        const int v = sh.nonb[wid + W * c];
-        if (v >= n && v < n + m) {
-          sh.yv[v - n] += double(tot);
-          sh.dyf[v - n] = tot;
-        }
-      }
-    }
-    __syncthreads();
-    for (int t = tid; t < m; t += NT) {
-      float s = 0.f;
-#pragma unroll
-      for (int w = 0; w < W; ++w) s += sh.part[w][t];
-      const int v = sh.basic[t];
-      const double dx = v >= n ? double(s) + sh.rr[v - n] : double(s);
-      sh.xb[t] += dx;
-      sh.dxf[t] = v < n ? float(dx) : 0.f;         // the structural part of the correction
-    }
-    __syncthreads();
-    // KKT certificate of the pair that is written out (x: the structural part
-    // of x_B; y: the slack duals): x >= 0, A x <= b, y >= 0, A^T y >= c and
-    // c^T x = b^T y, each to tol scaled by the data.  b - A x and A^T y - c at
-    // the corrected point are the FP64 values above plus FP32 products with
-    // the corrections, whose rounding (and the 2^-20 truncation of A) is
-    // bounded by 2^-15 times the sum of the products' magnitudes.
+    // Refinement rounds: FP64 residuals at the current point, one correction
+    // with the FP32 basis inverse, the certificate.  Almost every LP passes
+    // after the first round; one that fails gets up to two more rounds before
+    // it goes to the FP64 re-solve.
     const double tol = P.feas_tol, tp = tol * (1.0 + bmax), td = tol * (1.0 + cmax);
     constexpr float kDeltaErr = 1.f / 32768.f;
     int fail = 0;
-    for (int q = tid; q < nsb; q += NT) fail |= !(sh.xb[sh.sb[q]] >= -tp);
-    for (int p2 = tid; p2 < nns; p2 += NT) fail |= !(sh.yv[sh.kr[p2]] >= -td);
-    for (int i = tid; i < m; i += NT) {                 // slack b_i - A_i x of every row
-      float mag;
-      const float dl = row_delta(i, mag);
-      fail |= !(sh.sax[i] - double(dl + kDeltaErr * mag) >= -tp);
+    for (int round = 0;; ++round) {
+      // Residuals in FP64: sax = b - A x and r = sax - x_slack (rows, on the low
+      // threads); the reduced costs d = A^T y - c of every column (high
+      // threads), whose negatives on the basic structurals are the dual residual.
+      for (int i = tid; i < m; i += NT) {
+        const double ax = vin(sh.bin, i, dt) - row_dot(i);
+        const double r = sh.sp[i] >= 0 ? ax - sh.xb[sh.sp[i]] : ax;
+        sh.sax[i] = ax;
+        sh.rr[i] = r;
+        sh.rrf[i] = float(r);
+      }
+      for (int j = NT - 1 - tid; j < n; j += NT) {
+        const double d = col_dot(j) - vin(sh.cin, j, dt);
+        sh.dj[j] = d;
+        if (sh.posx[j] >= 0) sh.rhof[sh.posx[j]] = float(-d);
+      }
+      __syncthreads();
+      // Corrections with the FP32 basis inverse held in registers: its column for
+      // slack k is the tableau column of k when k is non-basic, else a unit vector.
+      {
+        constexpr int CP = pow2_at_least(C);
+        float coef[C];
+  #pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const int v = sh.nonb[wid + W * c];
+          coef[c] = (c < C - 1 || wid < W - 1) && v >= n && v < n + m ? sh.rrf[v - n] : 0.f;
+        }
+  #pragma unroll
+        for (int r = 0; r < R; ++r) {
+          float s = 0.f;
+  #pragma unroll
+          for (int c = 0; c < C; ++c) s = fmaf(T[r][c], coef[c], s);
+          sh.part[wid][lane + 32 * r] = s;
+        }
+        float rf[R];
+  #pragma unroll
+        for (int r = 0; r < R; ++r) rf[r] = sh.rhof[lane + 32 * r];
+        float dy[CP];
+  #pragma unroll
+        for (int c = 0; c < CP; ++c) {
+          float s = 0.f;
+          if (c < C) {
+  #pragma unroll
+            for (int r = 0; r < R; ++r) s = fmaf(T[r][c], rf[r], s);
+          }
+          dy[c] = s;
+        }
+        // Column sums across the lanes; lane l ends with column l / (32 / CP),
+        // and the first lane of each group applies it to y.
+        const float tot = reduce_scatter<CP>(dy, lane);
+        const int c = lane / (32 / CP);
+        if (lane % (32 / CP) == 0 && c < C && (c < C - 1 || wid < W - 1)) {
+          const int v = sh.nonb[wid + W * c];
+          if (v >= n && v < n + m) {
+            sh.yv[v - n] += double(tot);
+            sh.dyf[v - n] = tot;
+          }
+        }
+      }
+      __syncthreads();
+      for (int t = tid; t < m; t += NT) {
+        float s = 0.f;
+  #pragma unroll
+        for (int w = 0; w < W; ++w) s += sh.part[w][t];
+        const int v = sh.basic[t];
+        const double dx = v >= n ? double(s) + sh.rr[v - n] : double(s);
+        sh.xb[t] += dx;
+        sh.dxf[t] = v < n ? float(dx) : 0.f;         // the structural part of the correction
+      }
+      __syncthreads();
+      // KKT certificate of the pair that is written out (x: the structural part
+      // of x_B; y: the slack duals): x >= 0, A x <= b, y >= 0, A^T y >= c and
+      // c^T x = b^T y, each to tol scaled by the data.  b - A x and A^T y - c at
+      // the corrected point are the FP64 values above plus FP32 products with
+      // the corrections, whose rounding (and the 2^-20 truncation of A) is
+      // bounded by 2^-15 times the sum of the products' magnitudes.
+      fail = 0;
+      for (int q = tid; q < nsb; q += NT) fail |= !(sh.xb[sh.sb[q]] >= -tp);
+      for (int p2 = tid; p2 < nns; p2 += NT) fail |= !(sh.yv[sh.kr[p2]] >= -td);
+      for (int i = tid; i < m; i += NT) {                 // slack b_i - A_i x of every row
+        float mag;
+        const float dl = row_delta(i, mag);
+        fail |= !(sh.sax[i] - double(dl + kDeltaErr * mag) >= -tp);
+      }
+      for (int j = NT - 1 - tid; j < n; j += NT) {        // reduced cost A_j^T y - c_j of every column
+        float mag;
+        const float dl = col_delta(j, mag);
+        fail |= !(sh.dj[j] + double(dl - kDeltaErr * mag) >= -td);
+      }
+      // c^T x in warp 0 and b^T y in warp 1 (FP64).
+      if (wid == 0) {
+        double cx = 0.0;
+        for (int q = lane; q < nsb; q += 32) cx = fma(vin(sh.cin, sh.jb[q], dt), sh.xb[sh.sb[q]], cx);
+        cx = warp_sum(cx);
+        if (lane == 0) sh.red[0][0] = cx;
+      } else if (wid == 1) {
+        double by = 0.0;
+        for (int p2 = lane; p2 < nns; p2 += 32) by = fma(vin(sh.bin, sh.kr[p2], dt), sh.yv[sh.kr[p2]], by);
+        by = warp_sum(by);
+        if (lane == 0) sh.red[1][0] = by;
+      }
+      fail = __syncthreads_or(fail);
+      {
+        const double cx = sh.red[0][0], by = sh.red[1][0];
+        fail |= !(fabs(cx - by) <= tol * (1.0 + fabs(cx)));    // the duality gap (same value in every thread)
+      }
+      if (!fail || round == 2) break;
+      __syncthreads();       // sh.red and the check inputs are rewritten by the next round
     }
-    for (int j = NT - 1 - tid; j < n; j += NT) {        // reduced cost A_j^T y - c_j of every column
-      float mag;
-      const float dl = col_delta(j, mag);
-      fail |= !(sh.dj[j] + double(dl - kDeltaErr * mag) >= -td);
-    }
-    // c^T x in warp 0 and b^T y in warp 1 (FP64).
-    if (wid == 0) {
-      double cx = 0.0;
-      for (int q = lane; q < nsb; q += 32) cx = fma(vin(sh.cin, sh.jb[q], dt), sh.xb[sh.sb[q]], cx);
-      cx = warp_sum(cx);
-      if (lane == 0) sh.red[0][0] = cx;
-    } else if (wid == 1) {
-      double by = 0.0;
-      for (int p2 = lane; p2 < nns; p2 += 32) by = fma(vin(sh.bin, sh.kr[p2], dt), sh.yv[sh.kr[p2]], by);
-      by = warp_sum(by);
-      if (lane == 0) sh.red[1][0] = by;
-    }
-    fail = __syncthreads_or(fail);
     if (bp) for (int i = tid; i < m; i += NT) bp[i] = sh.basic[i];
-    if (!fail) {       // written now; a gap failure below sends the LP to the re-solve, which rewrites them
+    if (!fail) {
       for (int j = tid; j < n; j += NT) P.R.x[coff + j] = sh.posx[j] >= 0 ? sh.xb[sh.posx[j]] : 0.0;
       if (P.R.y) for (int k = tid; k < m; k += NT) P.R.y[boff + k] = sh.yv[k];
     }
     if (tid == 0) {
-      const double cx = sh.red[0][0], by = sh.red[1][0];
-      if (!fail && fabs(cx - by) <= tol * (1.0 + fabs(cx))) {
+      const double cx = sh.red[0][0];
+      if (!fail) {
         P.R.status[lp] = LPB_OPTIMAL;
         P.R.obj[lp] = cx;
       } else {

@@ -43,7 +43,7 @@ namespace {
 constexpr int kMaxThreads = 1024;
 
 struct Layout {
-  size_t tab, colb, rowb, basic, nonb, redv, redk, rcp, redf, sel, ins, xb, rr, yv, rho, sb, ns, sp, dj, jq, kq, total;
+  size_t tab, colb, rowb, basic, nonb, redv, redk, rcp, redf, sel, ins, wl, xb, rr, yv, rho, sb, ns, sp, dj, jq, kq, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -72,6 +72,7 @@ __host__ __device__ inline Layout make_layout(int eb, size_t tab, int max_m, int
   L.redf = o;  o = align16(o + 32 * 4);
   L.sel = o;   o = align16(o + 4 * 4);
   L.ins = o;   o = align16(o + size_t(max_n) + 2 * size_t(max_m) + 1);
+  L.wl = o;    o = align16(o + size_t(max_m) * 4 + 4);
   if (refine) {
     L.xb = o;  o = align16(o + size_t(max_m) * 8);
     L.rr = o;  o = align16(o + size_t(max_m) * 8);
@@ -106,6 +107,7 @@ struct Tab {
   float *redf;    // per-warp smallest FP32 ratio (FP64 Step 2)
   int *sel;       // Step 1 result for the next pivot: sel[0] = key or INT_MAX
   unsigned char *ins;
+  int *wl;        // warm start: columns whose variable enters
   int m, n, k, nc, ld;   // nc = n + k non-RHS columns; column nc is the RHS
   int nm;                // variables >= nm are artificial
   __device__ __forceinline__ T *row(int i) const {
@@ -236,14 +238,14 @@ __device__ __forceinline__ void update_any(const Tab<T> &S_, int rows, int l, in
 template <typename T>
 __device__ __forceinline__ void pivot(const Tab<T> &S_, int rows, int l, int e) {
   const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
-  T rp = T(0);
-  if ((threadIdx.x & 31) == 0) rp = T(1) / S.at(l, e);
-  rp = __shfl_sync(kFull, rp, 0);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {     // one division (FP64 divisions are slow here), published
+    S.rcp[32] = T(1) / S.at(l, e);
     const int v = S.basic[l];
     S.basic[l] = S.nonb[e];
     S.nonb[e] = v;
   }
+  __syncthreads();
+  const T rp = S.rcp[32];
   update_any(S, rows, l, e, rp);
   __syncthreads();
   pivot_finish(S, rows, l);
@@ -543,11 +545,14 @@ __device__ __forceinline__ bool warm_start(const Tab<T> &S_, const int32_t *warm
   __syncthreads();
   if (!s_ok) return false;
   const int rows = m + (S.k ? 2 : 1);
-  for (int t = 0; t < m; ++t) {
+  // Columns now holding a variable of the warm basis, found once: a pivot on
+  // column e changes only the variable of column e (to one outside the warm
+  // basis), so the list stays valid while its columns are pivoted in order.
+  __shared__ int s_nw;
+  const int nwl = compact(S.nc, S.wl, &s_nw, [&](int j) { const int v = S.nonb[j]; return v < nm && S.ins[v]; });
+  for (int t = 0; t < nwl; ++t) {
     __syncthreads();                              // reduction slots are free again
-    const int v = warm[t];
-    const int e = column_of(S, v, 0);
-    if (e < 0) continue;                          // already basic
+    const int e = S.wl[t];
     // Row with the largest |t_ie| among rows whose basic variable leaves.
     T bvv = pos_inf<T>();
     int key = INT_MAX;
@@ -824,6 +829,7 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
   S.redf = reinterpret_cast<float *>(smem + L.redf);
   S.sel = reinterpret_cast<int *>(smem + L.sel);
   S.ins = smem + L.ins;
+  S.wl = reinterpret_cast<int *>(smem + L.wl);
   __shared__ int s_item, s_k;
   __shared__ unsigned long long s_bmax, s_cmax;
   const T eps_p = T(P.eps_p), eps_d = T(P.eps_d);
