@@ -6,9 +6,10 @@ refinement and KKT certificate, FP64 re-solve of failures, outputs.  Prints one 
 (rank 0).  ``--impl reference`` times the CPU oracle on samples of the same workload.
 
 Secondary legs (skip with ``--no-legs``) time the other workloads once each with CUDA
-events: 1,000 x m=n=16; the m=n sweep; 10,000 x m=n=200 two-phase; hyperbox support
-functions (4,000,000 x 5 FP32, 6,000,000 x 28 FP64); 20,000 mixed sizes forward and
-forward+backward.
+events: 1,000 x m=n=16; the m=n sweep; the two Step 1 rules (most negative reduced cost
+vs a random eligible column) on 50,000 x m=n=100; 10,000 x m=n=200 two-phase; hyperbox
+support functions (4,000,000 x 5 FP32, 6,000,000 x 28 FP64); 20,000 mixed sizes forward
+and forward+backward.
 
 Launch: ``python bench.py --gpus 1 --steps K --warmup W``; for N > 1 under
 ``torch.distributed.run`` (one rank per GPU; each rank solves its own 50,000 LPs, weak
@@ -376,11 +377,13 @@ def secondary_legs(solver, dev):
     from paper_1609_08114_gb300 import LPBatch, solve
     out = {}
 
-    def solve_leg(name, batch, precs=("fp32_refine", "fp64"), reps=5):
+    def solve_leg(name, batch, precs=("fp32_refine", "fp64"), reps=5, **kw):
         res = solver.alloc_result(batch)
         leg = {"count": batch.count}
+        if kw:
+            leg["options"] = dict(kw)
         for prec in precs:
-            ms = _time(lambda: solver.solve(batch, prec=prec, out=res), reps=reps)
+            ms = _time(lambda: solver.solve(batch, prec=prec, out=res, **kw), reps=reps)
             st = res.status.cpu().numpy()
             leg[prec] = {"LPs_per_s": batch.count / (ms * 1e-3), "ms": ms,
                          "statuses": {str(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
@@ -394,6 +397,13 @@ def secondary_legs(solver, dev):
     for mn, cnt in ((5, 10_000), (28, 10_000), (50, 10_000), (200, 10_000), (300, 2_000)):
         solve_leg(f"type1_{cnt}x{mn}", _type1_device(cnt, mn, mn, dev, seed=mn), reps=3)
         torch.cuda.empty_cache()
+    # the paper's comparison of Step 1 rules (Section 5): the most negative reduced cost
+    # (LPC) against a random eligible column (RPC), same 50,000 x m=n=100 batch
+    bt = _type1_device(50_000, 100, 100, dev, seed=100)
+    solve_leg("type1_50000x100_lpc", bt, reps=3)
+    solve_leg("type1_50000x100_rpc", bt, reps=3, pivot_rule="rpc", seed=1)
+    del bt
+    torch.cuda.empty_cache()
     # 10,000 x m=n=200 two-phase
     sb = synth.type2(10_000, 200, 200, seed=2)
     solve_leg("type2_10000x200", LPBatch.from_packed(sb.m, sb.n, sb.A, sb.b, sb.c, device=dev), reps=3)

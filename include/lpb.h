@@ -107,7 +107,23 @@ typedef struct {
   int32_t kernel;            /* lpb_kernel: force a kernel class [LPB_KERNEL_AUTO] */
   int32_t threads;           /* threads per CTA of the tableau kernel, a multiple of 32 up to 1024 [auto] */
   int32_t reg_warps;         /* warps per LP of the register kernel, 4 or 8 [autotuned, else 8] */
+  int32_t pivot_rule;        /* lpb_pivot_rule: Step 1's entering-column rule [LPB_PIVOT_LPC] */
+  uint64_t seed;             /* LPB_PIVOT_RPC: seed of the counter-based random draw [0] */
 } lpb_options;
+
+/* Step 1's rule for the entering column (Section 4.2).
+ *   LPB_PIVOT_LPC: "largest positive coefficient" -- the most negative reduced
+ *     cost (Dantzig's rule), ties to the lowest variable index.
+ *   LPB_PIVOT_RPC: "random positive coefficient" -- a uniformly random eligible
+ *     column: the eligible variable j with the smallest (key, j), where the key
+ *     of j at pivot t of LP k (its index in the batch) is the upper 32 bits of
+ *     the first SplitMix64 output (Steele, Lea and Flood 2014) from the state
+ *     seed ^ (k << 40) ^ (t << 20) ^ j.  The draw is a function of (seed, k, t,
+ *     j) only, so FP64 solves repeat exactly; the FP32 register kernel ranks
+ *     eligible columns by the upper 31 bits of the same key.
+ * Under either rule, m + n consecutive degenerate pivots switch Step 1 to the
+ * lowest eligible variable index (Bland's rule) until a pivot makes progress. */
+typedef enum { LPB_PIVOT_LPC = 0, LPB_PIVOT_RPC = 1 } lpb_pivot_rule;
 
 typedef enum {
   LPB_KERNEL_AUTO = 0,

@@ -21,6 +21,9 @@ import subprocess
 import numpy as np
 
 OPTIMAL, INFEASIBLE, UNBOUNDED, ITER_LIMIT, NUMERIC = 0, 1, 2, 3, 4
+# Pivot rules of Section 4.2: most negative reduced cost (LPC, Dantzig) or a random eligible
+# column (RPC; the random draw is a counter-based SplitMix64 key, see simplex_oracle.c).
+LPC, RPC = 0, 1
 STATUS_NAMES = {0: "optimal", 1: "infeasible", 2: "unbounded", 3: "iter_limit", 4: "numeric"}
 
 # Tolerances of the FP64 oracle (the paper states none): absolute, on data of order 1.
@@ -55,6 +58,14 @@ def _declare(lib):
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.c_int, P, P, P, P, P, P]
     lib.oracle_max_threads.restype = ctypes.c_int
+    lib.oracle_solve_one_rule.restype = ctypes.c_int
+    lib.oracle_solve_one_rule.argtypes = lib.oracle_solve_one.argtypes + [ctypes.c_int, ctypes.c_uint64,
+                                                                          ctypes.c_int64]
+    lib.oracle_solve_batch_rule.restype = None
+    lib.oracle_solve_batch_rule.argtypes = lib.oracle_solve_batch.argtypes + [ctypes.c_int, ctypes.c_uint64,
+                                                                              ctypes.c_int64]
+    lib.oracle_splitmix64_next.restype = ctypes.c_uint64
+    lib.oracle_splitmix64_next.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
     return lib
 
 
@@ -79,8 +90,14 @@ def max_threads() -> int:
     return int(_load().oracle_max_threads())
 
 
+def splitmix64(state: int, count: int):
+    """The first ``count`` outputs of the oracle's SplitMix64 generator from ``state``."""
+    st = ctypes.c_uint64(state)
+    return [int(_load().oracle_splitmix64_next(ctypes.byref(st))) for _ in range(count)]
+
+
 def solve_one(A, b, c, max_iter: int = 0, eps_p: float = EPS_P, eps_d: float = EPS_D,
-              feas_tol: float = FEAS_TOL, lib=None):
+              feas_tol: float = FEAS_TOL, lib=None, rule: int = LPC, seed: int = 0, lp: int = 0):
     """Solve ``max c^T x, A x <= b, x >= 0`` for one LP.
 
     Returns a dict with ``status, x, y, obj, basis, iters, cert`` (``cert`` is a
@@ -94,18 +111,26 @@ def solve_one(A, b, c, max_iter: int = 0, eps_p: float = EPS_P, eps_d: float = E
     x = np.zeros(n); y = np.zeros(m); obj = np.zeros(1)
     basis = np.zeros(max(m, 1), dtype=np.int32); iters = np.zeros(1, dtype=np.int32)
     cert = np.zeros(n + m)
-    st = (lib or _load()).oracle_solve_one(m, n, _p(A), _p(b), _p(c), int(max_iter), eps_p, eps_d, feas_tol,
-                                  _p(x), _p(y), _p(obj), _p(basis), _p(iters), _p(cert))
+    L = lib or _load()
+    if rule == LPC:
+        st = L.oracle_solve_one(m, n, _p(A), _p(b), _p(c), int(max_iter), eps_p, eps_d, feas_tol,
+                                _p(x), _p(y), _p(obj), _p(basis), _p(iters), _p(cert))
+    else:
+        st = L.oracle_solve_one_rule(m, n, _p(A), _p(b), _p(c), int(max_iter), eps_p, eps_d, feas_tol,
+                                     _p(x), _p(y), _p(obj), _p(basis), _p(iters), _p(cert), int(rule),
+                                     int(seed), int(lp))
     return dict(status=int(st), x=x, y=y, obj=float(obj[0]), basis=basis[:m].copy(),
                 iters=int(iters[0]), cert=cert)
 
 
 def solve_batch(batch, max_iter: int = 0, eps_p: float = EPS_P, eps_d: float = EPS_D,
-                feas_tol: float = FEAS_TOL, nthreads: int = 0):
+                feas_tol: float = FEAS_TOL, nthreads: int = 0, rule: int = LPC, seed: int = 0,
+                first_lp: int = 0):
     """Solve every LP of a packed batch (``m, n, a_off, b_off, c_off, A, b, c``).
 
     Outputs follow the batch's packing: ``x`` like ``c``, ``y`` and ``basis`` like
-    ``b``, and one ``status``, ``obj`` and ``iters`` per LP.
+    ``b``, and one ``status``, ``obj`` and ``iters`` per LP.  Under ``rule=RPC`` LP k
+    of the batch draws its random keys as LP ``first_lp + k`` with ``seed``.
     """
     cnt = len(batch.m)
     m = np.ascontiguousarray(batch.m, dtype=np.int32)
@@ -120,7 +145,8 @@ def solve_batch(batch, max_iter: int = 0, eps_p: float = EPS_P, eps_d: float = E
     obj = np.zeros(cnt); x = np.zeros(c.size); y = np.zeros(b.size)
     basis = np.zeros(max(b.size, 1), dtype=np.int32)
     if cnt:
-        _load().oracle_solve_batch(cnt, _p(m), _p(n), _p(a_off), _p(b_off), _p(c_off), _p(A), _p(b), _p(c),
-                                   int(max_iter), eps_p, eps_d, feas_tol, int(nthreads),
-                                   _p(status), _p(x), _p(y), _p(obj), _p(basis), _p(iters))
+        _load().oracle_solve_batch_rule(cnt, _p(m), _p(n), _p(a_off), _p(b_off), _p(c_off), _p(A), _p(b),
+                                        _p(c), int(max_iter), eps_p, eps_d, feas_tol, int(nthreads),
+                                        _p(status), _p(x), _p(y), _p(obj), _p(basis), _p(iters), int(rule),
+                                        int(seed), int(first_lp))
     return dict(status=status, x=x, y=y, obj=obj, basis=basis[:b.size], iters=iters)

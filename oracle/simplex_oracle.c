@@ -26,7 +26,13 @@
  *     as -c).  The entering column is the most negative r_j below -eps_d, the
  *     paper's "largest coefficient" rule (LPC, Section 4.2) with the row's sign
  *     flipped.  Ties go to the lowest variable index.  No eligible column:
- *     optimal.
+ *     optimal.  Under the paper's "random positive coefficient" rule (RPC,
+ *     Section 4.2) the entering variable is a uniformly random eligible one:
+ *     the eligible variable j with the smallest (key, j), where the key of j
+ *     at pivot `it` of LP `lp` is the upper 32 bits of the first output of
+ *     SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) started from the state
+ *     seed ^ (lp << 40) ^ (it << 20) ^ j.  The random draw is thus a
+ *     counter-based function of the LP, the pivot and the variable.
  *   - Step 2 (leaving): among rows with pivot-column entry t_ie > eps_p, the
  *     minimum ratio b_i / t_ie.  Ties go to the lowest basic-variable index.
  *     No eligible row: unbounded.
@@ -67,6 +73,28 @@ typedef struct {
 
 #define TE(t, i, j) ((t)->T[(size_t)(i) * (t)->ld + (j)])
 
+enum { OR_RULE_LPC = 0, OR_RULE_RPC = 1 };
+typedef struct {
+  int rule;              /* OR_RULE_LPC or OR_RULE_RPC */
+  uint64_t seed;         /* RPC: generator seed */
+  uint64_t lp;           /* RPC: index of the LP in its batch */
+} pivot_rule;
+
+/* SplitMix64: advance the state by the golden-ratio increment and return the
+ * mixed output (the generator of Steele, Lea and Flood, OOPSLA 2014). */
+uint64_t oracle_splitmix64_next(uint64_t *state) {
+  uint64_t z = (*state += 0x9e3779b97f4a7c15ull);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+/* RPC key of variable j at pivot `it`. */
+static uint32_t rpc_key(const pivot_rule *pr, uint64_t it, uint64_t j) {
+  uint64_t st = pr->seed ^ (pr->lp << 40) ^ (it << 20) ^ j;
+  return (uint32_t)(oracle_splitmix64_next(&st) >> 32);
+}
+
 /* Step 3: pivot on (l, e). */
 static void pivot(tableau *t, int l, int e) {
   const int rows = t->m + 2, ld = t->ld;
@@ -85,17 +113,24 @@ static void pivot(tableau *t, int l, int e) {
   t->isbasic[e] = 1;
 }
 
-/* Step 1 on objective row `orow`; returns the entering column or -1 (optimal). */
-static int entering(const tableau *t, int orow, double eps_d, int bland) {
+/* Step 1 on objective row `orow` at pivot `it`; returns the entering column
+ * or -1 (optimal). */
+static int entering(const tableau *t, int orow, double eps_d, int bland, const pivot_rule *pr, int it) {
   const int nonart = t->n + t->m;
   int best = -1;
   double bv = 0.0;
+  uint32_t bk = 0;
   for (int j = 0; j < nonart; ++j) {
     if (t->isbasic[j]) continue;
     const double r = TE(t, orow, j);
     if (!(r < -eps_d)) continue;
     if (bland) return j;                  /* lowest eligible index */
-    if (best < 0 || r < bv) { best = j; bv = r; }
+    if (pr->rule == OR_RULE_RPC) {        /* smallest (key, j): j increases, so ties keep the lower j */
+      const uint32_t key = rpc_key(pr, (uint64_t)it, (uint64_t)j);
+      if (best < 0 || key < bk) { best = j; bk = key; }
+    } else if (best < 0 || r < bv) {
+      best = j; bv = r;
+    }
   }
   return best;
 }
@@ -119,10 +154,10 @@ static int leaving(const tableau *t, int e, double eps_p, double *theta) {
 
 /* Steps 1-3 iterated on objective row `orow` until a halt condition. */
 static int run_phase(tableau *t, int orow, int max_iter, int *iters, double eps_p, double eps_d,
-                     int *last_e) {
+                     int *last_e, const pivot_rule *pr) {
   int degenerate_run = 0, bland = 0;
   for (;;) {
-    const int e = entering(t, orow, eps_d, bland);
+    const int e = entering(t, orow, eps_d, bland, pr, *iters);
     if (e < 0) return OR_OPTIMAL;
     double theta;
     const int l = leaving(t, e, eps_p, &theta);
@@ -148,10 +183,10 @@ static int run_phase(tableau *t, int orow, int max_iter, int *iters, double eps_
  *   infeasible -> cert[0..m-1] = a Farkas vector u >= 0 with A^T u >= 0, b^T u < 0
  * Any output pointer may be NULL.  Returns the status.
  */
-int oracle_solve_one(int m, int n, const double *A, const double *b, const double *c,
-                     int max_iter, double eps_p, double eps_d, double feas_tol,
-                     double *x, double *y, double *obj, int *basis_out, int *iters_out,
-                     double *cert) {
+static int solve_one_rule(int m, int n, const double *A, const double *b, const double *c,
+                          int max_iter, double eps_p, double eps_d, double feas_tol,
+                          double *x, double *y, double *obj, int *basis_out, int *iters_out,
+                          double *cert, const pivot_rule *pr) {
   tableau t;
   int k = 0;
   for (int i = 0; i < m; ++i) k += (b[i] < 0.0);
@@ -197,7 +232,7 @@ int oracle_solve_one(int m, int n, const double *A, const double *b, const doubl
 
   int iters = 0, status = OR_OPTIMAL, last_e = -1;
   if (k > 0) {
-    status = run_phase(&t, m + 1, max_iter, &iters, eps_p, eps_d, &last_e);
+    status = run_phase(&t, m + 1, max_iter, &iters, eps_p, eps_d, &last_e, pr);
     if (status == OR_UNBOUNDED) status = OR_NUMERIC;   /* the auxiliary LP is bounded */
     if (status == OR_OPTIMAL) {
       const double w = TE(&t, m + 1, t.ncol);           /* = -(sum of artificials) */
@@ -223,7 +258,7 @@ int oracle_solve_one(int m, int n, const double *A, const double *b, const doubl
       }
     }
   }
-  if (status == OR_OPTIMAL) status = run_phase(&t, m, max_iter, &iters, eps_p, eps_d, &last_e);
+  if (status == OR_OPTIMAL) status = run_phase(&t, m, max_iter, &iters, eps_p, eps_d, &last_e, pr);
 
   if (status == OR_UNBOUNDED && cert) {
     /* The entering column with no eligible row gives the ray. */
@@ -256,29 +291,60 @@ int oracle_solve_one(int m, int n, const double *A, const double *b, const doubl
   return status;
 }
 
+int oracle_solve_one(int m, int n, const double *A, const double *b, const double *c,
+                     int max_iter, double eps_p, double eps_d, double feas_tol,
+                     double *x, double *y, double *obj, int *basis_out, int *iters_out,
+                     double *cert) {
+  const pivot_rule pr = {OR_RULE_LPC, 0, 0};
+  return solve_one_rule(m, n, A, b, c, max_iter, eps_p, eps_d, feas_tol, x, y, obj, basis_out, iters_out,
+                        cert, &pr);
+}
+
+/* oracle_solve_one under pivot rule `rule` (OR_RULE_LPC or OR_RULE_RPC with
+ * generator seed `seed`; `lp` is the LP's index in its batch). */
+int oracle_solve_one_rule(int m, int n, const double *A, const double *b, const double *c,
+                          int max_iter, double eps_p, double eps_d, double feas_tol,
+                          double *x, double *y, double *obj, int *basis_out, int *iters_out,
+                          double *cert, int rule, uint64_t seed, int64_t lp) {
+  const pivot_rule pr = {rule, seed, (uint64_t)lp};
+  return solve_one_rule(m, n, A, b, c, max_iter, eps_p, eps_d, feas_tol, x, y, obj, basis_out, iters_out,
+                        cert, &pr);
+}
+
 /*
  * A packed batch, one LP per entry: A at a_off[k] (m[k] x n[k] row-major), b at
  * b_off[k], c at c_off[k].  Outputs x at x_off[k] (= c_off), y at y_off[k]
  * (= b_off), basis at y_off[k].  The LPs are independent and are spread over
  * `nthreads` OpenMP threads (0 = the runtime's default).
  */
-void oracle_solve_batch(int count, const int32_t *m, const int32_t *n,
-                        const int64_t *a_off, const int64_t *b_off, const int64_t *c_off,
-                        const double *A, const double *b, const double *c,
-                        int max_iter, double eps_p, double eps_d, double feas_tol, int nthreads,
-                        int32_t *status, double *x, double *y, double *obj,
-                        int32_t *basis, int32_t *iters) {
+void oracle_solve_batch_rule(int count, const int32_t *m, const int32_t *n,
+                             const int64_t *a_off, const int64_t *b_off, const int64_t *c_off,
+                             const double *A, const double *b, const double *c,
+                             int max_iter, double eps_p, double eps_d, double feas_tol, int nthreads,
+                             int32_t *status, double *x, double *y, double *obj,
+                             int32_t *basis, int32_t *iters, int rule, uint64_t seed, int64_t first_lp) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
   for (int k = 0; k < count; ++k) {
     int it = 0;
-    status[k] = oracle_solve_one(m[k], n[k], A + a_off[k], b + b_off[k], c + c_off[k],
-                                 max_iter, eps_p, eps_d, feas_tol,
-                                 x + c_off[k], y + b_off[k], obj + k, basis + b_off[k], &it, NULL);
+    const pivot_rule pr = {rule, seed, (uint64_t)(first_lp + k)};
+    status[k] = solve_one_rule(m[k], n[k], A + a_off[k], b + b_off[k], c + c_off[k],
+                               max_iter, eps_p, eps_d, feas_tol,
+                               x + c_off[k], y + b_off[k], obj + k, basis + b_off[k], &it, NULL, &pr);
     iters[k] = it;
   }
+}
+
+void oracle_solve_batch(int count, const int32_t *m, const int32_t *n,
+                        const int64_t *a_off, const int64_t *b_off, const int64_t *c_off,
+                        const double *A, const double *b, const double *c,
+                        int max_iter, double eps_p, double eps_d, double feas_tol, int nthreads,
+                        int32_t *status, double *x, double *y, double *obj,
+                        int32_t *basis, int32_t *iters) {
+  oracle_solve_batch_rule(count, m, n, a_off, b_off, c_off, A, b, c, max_iter, eps_p, eps_d, feas_tol,
+                          nthreads, status, x, y, obj, basis, iters, OR_RULE_LPC, 0, 0);
 }
 
 int oracle_max_threads(void) {

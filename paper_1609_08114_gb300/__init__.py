@@ -27,6 +27,8 @@ __all__ = ["Solver", "LPBatch", "SolveResult", "LPBError", "OPTIMAL", "INFEASIBL
            "KERNEL_SMEM", "KERNEL_GMEM", "KERNEL_REG", "PRECISIONS"]
 
 PRECISIONS = {"fp64": FP64, "fp32_refine": FP32_REFINE, "fp32": FP32}
+# Step 1 rules of Section 4.2: most negative reduced cost, or a random eligible column.
+PIVOT_RULES = {"lpc": _lib.PIVOT_LPC, "rpc": _lib.PIVOT_RPC}
 
 
 def _ptr(t):
@@ -129,10 +131,12 @@ class Solver:
     # -- options / workspace ------------------------------------------------
     @staticmethod
     def options(prec="fp32_refine", max_iter=0, eps_p=0.0, eps_d=0.0, feas_tol=0.0, kernel=KERNEL_AUTO,
-                threads=0, keep_basis_inverse=0, reg_warps=0) -> _lib.Options:
+                threads=0, keep_basis_inverse=0, reg_warps=0, pivot_rule="lpc", seed=0) -> _lib.Options:
         p = PRECISIONS[prec] if isinstance(prec, str) else int(prec)
+        rule = PIVOT_RULES[pivot_rule] if isinstance(pivot_rule, str) else int(pivot_rule)
         return _lib.Options(p, int(max_iter), float(eps_p), float(eps_d), float(feas_tol),
-                            int(keep_basis_inverse), int(kernel), int(threads), int(reg_warps))
+                            int(keep_basis_inverse), int(kernel), int(threads), int(reg_warps), rule,
+                            int(seed) & 0xFFFFFFFFFFFFFFFF)
 
     def workspace_size(self, batch: LPBatch, opt: _lib.Options) -> int:
         n = ctypes.c_size_t()

@@ -22,6 +22,8 @@ FP64, FP32_REFINE, FP32 = 0, 1, 2
 DTYPE_F32, DTYPE_F64 = 0, 1
 # lpb_kernel
 KERNEL_AUTO, KERNEL_SMEM, KERNEL_GMEM, KERNEL_REG = 0, 1, 2, 3
+# lpb_pivot_rule
+PIVOT_LPC, PIVOT_RPC = 0, 1
 
 P = ctypes.c_void_p
 
@@ -40,7 +42,8 @@ class Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("eps_p", ctypes.c_double),
                 ("eps_d", ctypes.c_double), ("feas_tol", ctypes.c_double),
                 ("keep_basis_inverse", ctypes.c_int32), ("kernel", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("reg_warps", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("reg_warps", ctypes.c_int32), ("pivot_rule", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
 
 
 class Stats(ctypes.Structure):

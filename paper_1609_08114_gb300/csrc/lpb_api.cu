@@ -163,6 +163,7 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   if (b->dtype != LPB_DTYPE_F32 && b->dtype != LPB_DTYPE_F64) return LPB_EINVAL;
   if (o->prec < LPB_FP64 || o->prec > LPB_FP32) return LPB_EINVAL;
   if (o->max_iter < 0 || o->eps_p < 0 || o->eps_d < 0 || o->feas_tol < 0) return LPB_EINVAL;
+  if (o->pivot_rule != LPB_PIVOT_LPC && o->pivot_rule != LPB_PIVOT_RPC) return LPB_EINVAL;
   const bool fp32 = o->prec != LPB_FP64;
   pl->eps_p = o->eps_p > 0 ? o->eps_p : (fp32 ? 1e-6 : 1e-9);
   pl->eps_d = o->eps_d > 0 ? o->eps_d : (fp32 ? 1e-6 : 1e-9);
@@ -297,6 +298,8 @@ TableauParams base_params(int32_t *ctr, uint32_t *err, const lpb_batch *b, const
   p.eps_d = pl.eps_d;
   p.feas_tol = pl.feas_tol;
   p.err = err;
+  p.rule = o->pivot_rule;
+  p.seed = o->seed;
   return p;
 }
 

@@ -94,6 +94,18 @@ __device__ __forceinline__ double ld_as<double>(const void *p, int64_t i, int dt
   return ld_in(p, i, dt);
 }
 
+// Key of variable `var` at pivot `it` of LP `lp` under the random pivot rule:
+// the upper 32 bits of the first SplitMix64 output (Steele, Lea and Flood,
+// OOPSLA 2014) from the state seed ^ (lp << 40) ^ (it << 20) ^ var.
+__device__ __forceinline__ unsigned rpc_key(unsigned long long seed, int lp, int it, int var) {
+  unsigned long long z = (seed ^ (static_cast<unsigned long long>(lp) << 40) ^
+                          (static_cast<unsigned long long>(it) << 20) ^ static_cast<unsigned long long>(var)) +
+                         0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return unsigned((z ^ (z >> 31)) >> 32);
+}
+
 // (value, key) order: smaller value first, then smaller key.
 template <typename T>
 __device__ __forceinline__ void keep_better(T &v, int &k, T ov, int ok) {
@@ -230,6 +242,8 @@ struct TableauParams {
   int max_iter;                // 0: 50 (m + n)
   double eps_p, eps_d, feas_tol;
   uint32_t *err;
+  int rule;                    // lpb_pivot_rule
+  unsigned long long seed;     // LPB_PIVOT_RPC seed
 };
 
 struct BackwardParams {

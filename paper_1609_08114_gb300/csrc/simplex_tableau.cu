@@ -253,16 +253,32 @@ __device__ __forceinline__ void pivot(const Tab<T> &S_, int rows, int l, int e) 
 }
 
 // Step 1 over objective row `orow` in one warp (every lane gets the result):
-// the most negative reduced cost below -eps_d over enterable columns (the
-// lowest variable index under Bland's rule).  Column `ecol` is taken to hold
-// variable `evar` (a pivot whose swap of nonb may not be visible yet).
+// eligible columns are those with a reduced cost below -eps_d; the most
+// negative one enters (LPC), or the one with the smallest random key at pivot
+// `it` (RPC), or the lowest variable index under Bland's rule.  Column `ecol`
+// is taken to hold variable `evar` (a pivot whose swap of nonb may not be
+// visible yet).  Keys are (variable << kIdxBits) | column.
 template <typename T>
 __device__ __forceinline__ void step1_warp(const Tab<T> &S_, int orow, bool bland, T eps_d, int ecol, int evar,
-                                           T &v, int &key) {
+                                           T &v, int &key, int rule, unsigned long long seed, int lp, int it) {
   const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
   const T *r = S.row(orow);
   v = pos_inf<T>();
   key = INT_MAX;
+  if (rule == LPB_PIVOT_RPC && !bland) {
+    unsigned best = 0xffffffffu;
+    for (int j = threadIdx.x & 31; j < S.nc; j += 32) {
+      const int var = j == ecol ? evar : S.nonb[j];
+      if (var >= S.nm || !(r[j] < -eps_d)) continue;
+      const unsigned k = rpc_key(seed, lp, it, var);
+      const int kk = (var << kIdxBits) | j;
+      if (k < best || (k == best && kk < key)) { best = k; key = kk; }
+    }
+    const unsigned mk = __reduce_min_sync(kFull, best);
+    key = int(__reduce_min_sync(kFull, best == mk ? unsigned(key) : 0xffffffffu));   // INT_MAX if none
+    v = T(0);
+    return;
+  }
   for (int j = threadIdx.x & 31; j < S.nc; j += 32) {
     const int var = j == ecol ? evar : S.nonb[j];
     if (var >= S.nm) continue;
@@ -277,7 +293,7 @@ __device__ __forceinline__ void step1_warp(const Tab<T> &S_, int orow, bool blan
 // skips them (they are redundant rows left after Phase I).
 template <typename T>
 __device__ __forceinline__ int run_phase(const Tab<T> &S_, int orow, int rows, int phase, int &iters, int max_iter,
-                         T eps_p, T eps_d) {
+                         T eps_p, T eps_d, int rule, unsigned long long seed, int lp) {
   const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int r0, r1;
@@ -289,7 +305,7 @@ __device__ __forceinline__ int run_phase(const Tab<T> &S_, int orow, int rows, i
   if (w == 0) {            // Step 1 of the first pivot
     T v;
     int key;
-    step1_warp(S, orow, false, eps_d, -1, 0, v, key);
+    step1_warp(S, orow, false, eps_d, -1, 0, v, key, rule, seed, lp, iters);
     if (lane == 0) S.sel[0] = key;
   }
   __syncthreads();
@@ -378,7 +394,7 @@ __device__ __forceinline__ int run_phase(const Tab<T> &S_, int orow, int rows, i
       __syncwarp();
       T v;
       int key;
-      step1_warp(S, orow, bland, eps_d, e, leave, v, key);
+      step1_warp(S, orow, bland, eps_d, e, leave, v, key, rule, seed, lp, iters);
       if (lane == 0) S.sel[0] = key;
     }
     __syncthreads();
@@ -919,7 +935,7 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
         const double w0 = -double(S.at(m + 1, S.nc));
         const double ftol = sizeof(T) == 4 ? fmax(P.feas_tol * (1.0 + bmax), 1e-5 * (1.0 + w0))
                                            : P.feas_tol * (1.0 + bmax);
-        status = run_phase(S, m + 1, m + 2, 1, iters, max_iter, eps_p, eps_d);
+        status = run_phase(S, m + 1, m + 2, 1, iters, max_iter, eps_p, eps_d, P.rule, P.seed, lp);
         if (status == LPB_OPTIMAL) {
           const double w = double(S.at(m + 1, S.nc));
           if (-w > ftol) {
@@ -934,7 +950,7 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
           }
         }
       }
-      if (status == LPB_OPTIMAL) status = run_phase(S, m, m + 1, 2, iters, max_iter, eps_p, eps_d);
+      if (status == LPB_OPTIMAL) status = run_phase(S, m, m + 1, 2, iters, max_iter, eps_p, eps_d, P.rule, P.seed, lp);
     }
     if constexpr (sizeof(T) == 4) if (P.mode == MODE_FP32_REFINE) {
       bool done = false;

@@ -59,7 +59,7 @@ def test_struct_layouts_match_header(tmp_path):
         "lpb_batch": (_lib.Batch, ["count", "max_m", "max_n", "dtype", "m", "n", "a_off", "b_off", "c_off", "A", "b", "c"]),
         "lpb_result": (_lib.Result, ["status", "iters", "obj", "x", "y", "basis"]),
         "lpb_options": (_lib.Options, ["prec", "max_iter", "eps_p", "eps_d", "feas_tol", "keep_basis_inverse",
-                                       "kernel", "threads", "reg_warps"]),
+                                       "kernel", "threads", "reg_warps", "pivot_rule", "seed"]),
         "lpb_stats": (_lib.Stats, ["resolved_fp64", "deferred", "kernels", "reserved"]),
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lpb.h"', "int main(void){"]
