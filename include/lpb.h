@@ -203,6 +203,27 @@ typedef struct {
 } lpb_stats;
 lpb_err lpb_get_stats(lpb_handle *handle, void *stream, lpb_stats *stats);
 
+/* lpb_solve for a batch and results held in HOST memory: the CUDA-streams
+ * pipeline of Section 4.5.  `host_batch` and `host_result` have the layout of
+ * lpb_batch / lpb_result, but every pointer in them is a host pointer; the
+ * offsets must increase with the LP index (each array packed in LP order, no
+ * overlap; LPB_EINVAL otherwise).  The batch is cut into chunks of `chunk`
+ * LPs; while chunk i is solved on `stream`, chunk i+1 is copied to the device
+ * and chunk i-1's results are copied back, on two streams of the handle.  Host
+ * arrays should be page-locked (cudaHostAlloc / cudaHostRegister) for the
+ * copies to overlap; pageable memory works but serialises the copies with the
+ * host.  `ws` is device memory of at least lpb_workspace_size_host() bytes,
+ * 256-byte aligned: one solve workspace and two chunk buffer sets.  The call
+ * queues the work and returns; `stream` reaches the point after the call once
+ * every result is in host memory (synchronise it before reading them).  The
+ * results equal those of lpb_solve on the same batch (LPB_PIVOT_RPC keys LPs
+ * by their batch index).  A CUDA error after some chunks were queued returns
+ * LPB_ECUDA with those chunks' work still in flight. */
+lpb_err lpb_workspace_size_host(lpb_handle *handle, const lpb_batch *host_batch, const lpb_options *opt,
+                                int32_t chunk, size_t *bytes);
+lpb_err lpb_solve_host(lpb_handle *handle, const lpb_batch *host_batch, const lpb_options *opt,
+                       const lpb_result *host_result, int32_t chunk, void *ws, size_t ws_bytes, void *stream);
+
 /* lpb_solve for callers that cannot allocate device memory.  The paper has no
  * counterpart; this exists for plug-ins whose host framework owns all device
  * memory through its own pool, and for loops where cudaMalloc / cudaFree are

@@ -74,6 +74,11 @@ class LPBatch:
                    max_m if max_m is not None else (int(m.max()) if len(m) else 1),
                    max_n if max_n is not None else (int(n.max()) if len(n) else 1))
 
+    def pin_memory(self) -> "LPBatch":
+        """A copy of a host batch in page-locked memory (for ``Solver.solve_host``)."""
+        t = [x.pin_memory() for x in (self.m, self.n, self.a_off, self.b_off, self.c_off, self.A, self.b, self.c)]
+        return LPBatch(*t, self.max_m, self.max_n)
+
     @classmethod
     def from_dense(cls, A: torch.Tensor, b: torch.Tensor, c: torch.Tensor):
         """Fixed-size batch from device tensors ``A[count, m, n]``, ``b[count, m]``, ``c[count, n]``."""
@@ -168,6 +173,31 @@ class Solver:
         cb, cr = batch.cstruct(), res.cstruct()
         _lib.check(self.lib.lpb_solve(self.h, ctypes.byref(cb), ctypes.byref(opt), ctypes.byref(cr),
                                       _ptr(ws), ws.numel(), _stream_handle(self.device)), "lpb_solve")
+        return res
+
+    def alloc_host_result(self, batch: LPBatch) -> SolveResult:
+        """Page-locked host result arrays for ``solve_host``."""
+        pin = lambda n, dt: torch.empty(n, dtype=dt).pin_memory()
+        return SolveResult(pin(batch.count, torch.int32), pin(batch.count, torch.int32),
+                           pin(batch.count, torch.float64), pin(batch.c.numel(), torch.float64),
+                           pin(batch.b.numel(), torch.float64), pin(batch.b.numel(), torch.int32))
+
+    def solve_host(self, batch: LPBatch, prec="fp32_refine", chunk: int = 8192, out: SolveResult | None = None,
+                   **kw) -> SolveResult:
+        """Solve a batch held in (page-locked) host memory through the chunked copy / solve /
+        copy-back pipeline of lpb_solve_host, on the current stream (asynchronous: synchronise
+        the stream before reading the results)."""
+        if batch.A.device.type != "cpu":
+            raise ValueError("solve_host takes a batch in host memory (LPBatch.from_packed(..., device='cpu'))")
+        opt = self.options(prec, **kw)
+        res = out if out is not None else self.alloc_host_result(batch)
+        cb, cr = batch.cstruct(), res.cstruct()
+        n = ctypes.c_size_t()
+        _lib.check(self.lib.lpb_workspace_size_host(self.h, ctypes.byref(cb), ctypes.byref(opt), int(chunk),
+                                                    ctypes.byref(n)), "lpb_workspace_size_host")
+        ws = self.workspace(int(n.value))
+        _lib.check(self.lib.lpb_solve_host(self.h, ctypes.byref(cb), ctypes.byref(opt), ctypes.byref(cr), int(chunk),
+                                           _ptr(ws), ws.numel(), _stream_handle(self.device)), "lpb_solve_host")
         return res
 
     def autotune(self, batch: LPBatch, prec="fp32_refine", table_path: str | None = None,

@@ -61,6 +61,10 @@ SIGNATURES = {
                                  P, ctypes.c_size_t, P]),
     "lpb_solve_backward": (ctypes.c_int, [P, ctypes.POINTER(Batch), ctypes.POINTER(Options),
                                           ctypes.POINTER(Result), P, P, P, P, P, P, ctypes.c_size_t, P]),
+    "lpb_workspace_size_host": (ctypes.c_int, [P, ctypes.POINTER(Batch), ctypes.POINTER(Options), ctypes.c_int32,
+                                               ctypes.POINTER(ctypes.c_size_t)]),
+    "lpb_solve_host": (ctypes.c_int, [P, ctypes.POINTER(Batch), ctypes.POINTER(Options), ctypes.POINTER(Result),
+                                      ctypes.c_int32, P, ctypes.c_size_t, P]),
     "lpb_hyperbox": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P, P,
                                     ctypes.c_int32, P, P, P]),
     "lpb_autotune": (ctypes.c_int, [P, ctypes.POINTER(Batch), ctypes.POINTER(Options), ctypes.POINTER(Result), P,

@@ -31,6 +31,11 @@ struct lpb_handle {
     int kernel, threads, reg_warps;
   };
   std::vector<Tuned> tuned;
+  // Host-memory pipeline (lpb_solve_host): copy-in and copy-out streams and
+  // events per buffer set (input ready, solve done, results out) plus a start
+  // event on the caller's stream.
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[2] = {}, ev_comp[2] = {}, ev_out[2] = {}, ev_start = nullptr;
 };
 
 namespace {
@@ -320,7 +325,7 @@ lpb_err solve_workspace_bytes(const DeviceInfo &d, const lpb_batch *b, const lpb
 
 lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_batch *b,
                   const lpb_options *o, const lpb_result *r, void *ws, size_t ws_bytes, cudaStream_t s,
-                  cudaEvent_t *prof_ev, bool *prof_ran, int *kernels) {
+                  cudaEvent_t *prof_ev, bool *prof_ran, int *kernels, long long lp_base) {
   if (kernels) *kernels = 0;
   Plan pl;
   lpb_err e = make_plan(d, b, o, r->basis != nullptr, &pl);
@@ -357,6 +362,7 @@ lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_ba
       }
     }
     TableauParams p = base_params(ctr, err, b, r, o, pl, w);
+    p.lp_base = lp_base;
     p.kcap = ps.kcap;
     p.mode = ps.mode;
     p.slot_bytes = ps.slot_bytes;
@@ -392,6 +398,95 @@ lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_ba
 
 }  // namespace lpb
 
+// ---- host-memory pipeline (Section 4.5: CUDA streams) ----------------------
+
+namespace {
+
+// Rebases the offsets of a chunk to its own buffers.
+__global__ void rebase_offsets(int64_t *a_off, int64_t *b_off, int64_t *c_off, int cnt, int64_t a0, int64_t b0,
+                               int64_t c0) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+    a_off[k] -= a0;
+    b_off[k] -= b0;
+    c_off[k] -= c0;
+  }
+}
+
+// Chunks of a host batch: LP ranges, their element ranges in A, b, c, and the
+// carving of the workspace into one solve workspace and two buffer sets.
+struct HostPlan {
+  int chunk = 0, nchunk = 0;
+  size_t a_max = 0, b_max = 0, c_max = 0;   // largest element ranges of a chunk
+  size_t solve_ws = 0;
+  size_t set_bytes = 0;
+  size_t o_A = 0, o_b = 0, o_c = 0, o_m = 0, o_n = 0, o_ao = 0, o_bo = 0, o_co = 0;
+  size_t o_st = 0, o_it = 0, o_obj = 0, o_x = 0, o_y = 0, o_bs = 0;
+  size_t total = 0;
+};
+
+// Element range [lo, hi) of LPs k0..k1-1 in an array with offsets `off` and
+// lengths len(k).
+template <typename F>
+void chunk_range(const int64_t *off, int k0, int k1, F len, int64_t *lo, int64_t *hi) {
+  *lo = off[k0];
+  *hi = off[k1 - 1] + len(k1 - 1);
+}
+
+lpb_err make_host_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o, int chunk, HostPlan *hp) {
+  if (!b || !o || chunk < 1) return LPB_EINVAL;
+  if (b->count < 0) return LPB_EINVAL;
+  if (b->count > 0 && (!b->m || !b->n || !b->a_off || !b->b_off || !b->c_off || !b->A || !b->b || !b->c))
+    return LPB_EINVAL;
+  const int cnt = b->count;
+  hp->chunk = cnt > 0 && chunk > cnt ? cnt : chunk;
+  hp->nchunk = cnt > 0 ? (cnt + hp->chunk - 1) / hp->chunk : 0;
+  // Offsets must follow the LP order with no overlap (each array packed in order).
+  for (int k = 0; k < cnt; ++k) {
+    const int64_t mk = b->m[k], nk = b->n[k];
+    if (mk < 0 || nk < 0 || b->a_off[k] < 0 || b->b_off[k] < 0 || b->c_off[k] < 0) return LPB_EINVAL;
+    if (k + 1 < cnt && (b->a_off[k + 1] < b->a_off[k] + mk * nk || b->b_off[k + 1] < b->b_off[k] + mk ||
+                        b->c_off[k + 1] < b->c_off[k] + nk))
+      return LPB_EINVAL;
+  }
+  for (int i = 0; i < hp->nchunk; ++i) {
+    const int k0 = i * hp->chunk, k1 = (k0 + hp->chunk < cnt) ? k0 + hp->chunk : cnt;
+    int64_t lo, hi;
+    chunk_range(b->a_off, k0, k1, [&](int k) { return int64_t(b->m[k]) * b->n[k]; }, &lo, &hi);
+    if (size_t(hi - lo) > hp->a_max) hp->a_max = size_t(hi - lo);
+    chunk_range(b->b_off, k0, k1, [&](int k) { return int64_t(b->m[k]); }, &lo, &hi);
+    if (size_t(hi - lo) > hp->b_max) hp->b_max = size_t(hi - lo);
+    chunk_range(b->c_off, k0, k1, [&](int k) { return int64_t(b->n[k]); }, &lo, &hi);
+    if (size_t(hi - lo) > hp->c_max) hp->c_max = size_t(hi - lo);
+  }
+  lpb_batch cb = *b;
+  cb.count = hp->chunk;
+  const lpb_err e = solve_workspace_bytes(d, &cb, o, false, &hp->solve_ws);
+  if (e != LPB_OK) return e;
+  const size_t es = b->dtype == LPB_DTYPE_F64 ? 8 : 4;
+  const size_t ch = size_t(hp->chunk);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t at = off; off = align256(off + (bytes ? bytes : 1)); return at; };
+  hp->o_A = take(hp->a_max * es);
+  hp->o_b = take(hp->b_max * es);
+  hp->o_c = take(hp->c_max * es);
+  hp->o_m = take(ch * 4);
+  hp->o_n = take(ch * 4);
+  hp->o_ao = take(ch * 8);
+  hp->o_bo = take(ch * 8);
+  hp->o_co = take(ch * 8);
+  hp->o_st = take(ch * 4);
+  hp->o_it = take(ch * 4);
+  hp->o_obj = take(ch * 8);
+  hp->o_x = take(hp->c_max * 8);
+  hp->o_y = take(hp->b_max * 8);
+  hp->o_bs = take(hp->b_max * 4);
+  hp->set_bytes = off;
+  hp->total = align256(hp->solve_ws) + 2 * hp->set_bytes;
+  return LPB_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *lpb_version(void) { return "liblpb 0.1 (sm_103a)"; }
@@ -426,9 +521,25 @@ lpb_err lpb_create(lpb_handle **handle, int device) {
   if (e == cudaSuccess) e = cudaMalloc(&h->d_ctr, CTR_N * sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(h->d_err, 0, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(h->d_ctr, 0, CTR_N * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking);
+  for (int j = 0; j < 2 && e == cudaSuccess; ++j) {
+    e = cudaEventCreateWithFlags(&h->ev_in[j], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_comp[j], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_out[j], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaFree(h->d_err);
     cudaFree(h->d_ctr);
+    for (int j = 0; j < 2; ++j) {
+      if (h->ev_in[j]) cudaEventDestroy(h->ev_in[j]);
+      if (h->ev_comp[j]) cudaEventDestroy(h->ev_comp[j]);
+      if (h->ev_out[j]) cudaEventDestroy(h->ev_out[j]);
+    }
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->s_in) cudaStreamDestroy(h->s_in);
+    if (h->s_out) cudaStreamDestroy(h->s_out);
     delete h;
     return LPB_ECUDA;
   }
@@ -447,6 +558,14 @@ lpb_err lpb_destroy(lpb_handle *h) {
       for (int i = 0; i < lpb_handle::kProfMax * 3 * 2; ++i) cudaEventDestroy(h->prof_ev[i]);
       delete[] h->prof_ev;
     }
+    for (int j = 0; j < 2; ++j) {
+      cudaEventDestroy(h->ev_in[j]);
+      cudaEventDestroy(h->ev_comp[j]);
+      cudaEventDestroy(h->ev_out[j]);
+    }
+    cudaEventDestroy(h->ev_start);
+    cudaStreamDestroy(h->s_in);
+    cudaStreamDestroy(h->s_out);
   }
   delete h;
   return LPB_OK;
@@ -496,6 +615,112 @@ lpb_err lpb_solve(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const
                               prof ? h->prof_ran + h->prof_n * 3 : nullptr, &h->last_kernels);
   if (e == LPB_OK && prof) ++h->prof_n;
   return e;
+}
+
+lpb_err lpb_workspace_size_host(lpb_handle *h, const lpb_batch *b, const lpb_options *o, int32_t chunk,
+                                size_t *bytes) {
+  if (!h || !b || !o || !bytes) return LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  HostPlan hp;
+  const lpb_err e = make_host_plan(device_info(h), b, o, chunk, &hp);
+  if (e != LPB_OK) return e;
+  *bytes = hp.total;
+  return LPB_OK;
+}
+
+lpb_err lpb_solve_host(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const lpb_result *r, int32_t chunk,
+                       void *ws, size_t ws_bytes, void *stream) {
+  if (!h || !b || !o || !r) return LPB_EINVAL;
+  if (b->count == 0) return b->count < 0 ? LPB_EINVAL : LPB_OK;
+  if (!r->status || !r->obj || !r->x) return LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  const DeviceInfo d = device_info(h);
+  HostPlan hp;
+  lpb_err e = make_host_plan(d, b, o, chunk, &hp);
+  if (e != LPB_OK) return e;
+  if (ws_bytes < hp.total || !ws) return LPB_ENOMEM;
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return LPB_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char *w = static_cast<unsigned char *>(ws);
+  unsigned char *solve_ws = w;
+  unsigned char *sets[2] = {w + align256(hp.solve_ws), w + align256(hp.solve_ws) + hp.set_bytes};
+  const size_t es = b->dtype == LPB_DTYPE_F64 ? 8 : 4;
+  auto ok = [](cudaError_t ce) { return ce == cudaSuccess; };
+  // Work already queued on the caller's stream may still use the workspace.
+  if (!ok(cudaEventRecord(h->ev_start, s)) || !ok(cudaStreamWaitEvent(h->s_in, h->ev_start, 0)) ||
+      !ok(cudaStreamWaitEvent(h->s_out, h->ev_start, 0)))
+    return LPB_ECUDA;
+  const unsigned char *hA = static_cast<const unsigned char *>(b->A), *hb = static_cast<const unsigned char *>(b->b),
+                      *hc = static_cast<const unsigned char *>(b->c);
+  for (int i = 0; i < hp.nchunk; ++i) {
+    const int j = i & 1;
+    unsigned char *set = sets[j];
+    const int k0 = i * hp.chunk, k1 = (k0 + hp.chunk < b->count) ? k0 + hp.chunk : b->count, cnt = k1 - k0;
+    int64_t a0, a1, b0, b1, c0, c1;
+    chunk_range(b->a_off, k0, k1, [&](int k) { return int64_t(b->m[k]) * b->n[k]; }, &a0, &a1);
+    chunk_range(b->b_off, k0, k1, [&](int k) { return int64_t(b->m[k]); }, &b0, &b1);
+    chunk_range(b->c_off, k0, k1, [&](int k) { return int64_t(b->n[k]); }, &c0, &c1);
+    // Copy in: once the solve of chunk i - 2 has consumed this buffer set.
+    if (i >= 2 && !ok(cudaStreamWaitEvent(h->s_in, h->ev_comp[j], 0))) return LPB_ECUDA;
+    const bool in_ok =
+        ok(cudaMemcpyAsync(set + hp.o_A, hA + size_t(a0) * es, size_t(a1 - a0) * es, cudaMemcpyHostToDevice, h->s_in)) &&
+        ok(cudaMemcpyAsync(set + hp.o_b, hb + size_t(b0) * es, size_t(b1 - b0) * es, cudaMemcpyHostToDevice, h->s_in)) &&
+        ok(cudaMemcpyAsync(set + hp.o_c, hc + size_t(c0) * es, size_t(c1 - c0) * es, cudaMemcpyHostToDevice, h->s_in)) &&
+        ok(cudaMemcpyAsync(set + hp.o_m, b->m + k0, size_t(cnt) * 4, cudaMemcpyHostToDevice, h->s_in)) &&
+        ok(cudaMemcpyAsync(set + hp.o_n, b->n + k0, size_t(cnt) * 4, cudaMemcpyHostToDevice, h->s_in)) &&
+        ok(cudaMemcpyAsync(set + hp.o_ao, b->a_off + k0, size_t(cnt) * 8, cudaMemcpyHostToDevice, h->s_in)) &&
+        ok(cudaMemcpyAsync(set + hp.o_bo, b->b_off + k0, size_t(cnt) * 8, cudaMemcpyHostToDevice, h->s_in)) &&
+        ok(cudaMemcpyAsync(set + hp.o_co, b->c_off + k0, size_t(cnt) * 8, cudaMemcpyHostToDevice, h->s_in));
+    if (!in_ok) return LPB_ECUDA;
+    rebase_offsets<<<(cnt + 255) / 256, 256, 0, h->s_in>>>(
+        reinterpret_cast<int64_t *>(set + hp.o_ao), reinterpret_cast<int64_t *>(set + hp.o_bo),
+        reinterpret_cast<int64_t *>(set + hp.o_co), cnt, a0, b0, c0);
+    if (!ok(cudaGetLastError()) || !ok(cudaEventRecord(h->ev_in[j], h->s_in))) return LPB_ECUDA;
+    // Solve on the caller's stream, once the inputs are in and the results of
+    // chunk i - 2 have left this buffer set.
+    if (!ok(cudaStreamWaitEvent(s, h->ev_in[j], 0))) return LPB_ECUDA;
+    if (i >= 2 && !ok(cudaStreamWaitEvent(s, h->ev_out[j], 0))) return LPB_ECUDA;
+    lpb_batch cb = *b;
+    cb.count = cnt;
+    cb.m = reinterpret_cast<const int32_t *>(set + hp.o_m);
+    cb.n = reinterpret_cast<const int32_t *>(set + hp.o_n);
+    cb.a_off = reinterpret_cast<const int64_t *>(set + hp.o_ao);
+    cb.b_off = reinterpret_cast<const int64_t *>(set + hp.o_bo);
+    cb.c_off = reinterpret_cast<const int64_t *>(set + hp.o_co);
+    cb.A = set + hp.o_A;
+    cb.b = set + hp.o_b;
+    cb.c = set + hp.o_c;
+    lpb_result cr{};
+    cr.status = reinterpret_cast<int32_t *>(set + hp.o_st);
+    cr.iters = r->iters ? reinterpret_cast<int32_t *>(set + hp.o_it) : nullptr;
+    cr.obj = reinterpret_cast<double *>(set + hp.o_obj);
+    cr.x = reinterpret_cast<double *>(set + hp.o_x);
+    cr.y = r->y ? reinterpret_cast<double *>(set + hp.o_y) : nullptr;
+    cr.basis = r->basis ? reinterpret_cast<int32_t *>(set + hp.o_bs) : nullptr;
+    e = run_solve(d, h->d_ctr, h->d_err, &cb, o, &cr, solve_ws, hp.solve_ws, s, nullptr, nullptr,
+                  &h->last_kernels, k0);
+    if (e != LPB_OK) return e;
+    if (!ok(cudaEventRecord(h->ev_comp[j], s))) return LPB_ECUDA;
+    // Copy out.
+    if (!ok(cudaStreamWaitEvent(h->s_out, h->ev_comp[j], 0))) return LPB_ECUDA;
+    bool out_ok =
+        ok(cudaMemcpyAsync(r->status + k0, cr.status, size_t(cnt) * 4, cudaMemcpyDeviceToHost, h->s_out)) &&
+        ok(cudaMemcpyAsync(r->obj + k0, cr.obj, size_t(cnt) * 8, cudaMemcpyDeviceToHost, h->s_out)) &&
+        ok(cudaMemcpyAsync(r->x + c0, cr.x, size_t(c1 - c0) * 8, cudaMemcpyDeviceToHost, h->s_out));
+    if (out_ok && r->iters)
+      out_ok = ok(cudaMemcpyAsync(r->iters + k0, cr.iters, size_t(cnt) * 4, cudaMemcpyDeviceToHost, h->s_out));
+    if (out_ok && r->y)
+      out_ok = ok(cudaMemcpyAsync(r->y + b0, cr.y, size_t(b1 - b0) * 8, cudaMemcpyDeviceToHost, h->s_out));
+    if (out_ok && r->basis)
+      out_ok = ok(cudaMemcpyAsync(r->basis + b0, cr.basis, size_t(b1 - b0) * 4, cudaMemcpyDeviceToHost, h->s_out));
+    if (!out_ok || !ok(cudaEventRecord(h->ev_out[j], h->s_out))) return LPB_ECUDA;
+  }
+  // The caller's stream passes this point once every result is in host memory.
+  for (int j = 0; j < 2 && j < hp.nchunk; ++j)
+    if (!ok(cudaStreamWaitEvent(s, h->ev_out[j], 0))) return LPB_ECUDA;
+  return LPB_OK;
 }
 
 lpb_err lpb_autotune(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const lpb_result *r,

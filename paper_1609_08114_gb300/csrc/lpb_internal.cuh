@@ -97,7 +97,7 @@ __device__ __forceinline__ double ld_as<double>(const void *p, int64_t i, int dt
 // Key of variable `var` at pivot `it` of LP `lp` under the random pivot rule:
 // the upper 32 bits of the first SplitMix64 output (Steele, Lea and Flood,
 // OOPSLA 2014) from the state seed ^ (lp << 40) ^ (it << 20) ^ var.
-__device__ __forceinline__ unsigned rpc_key(unsigned long long seed, int lp, int it, int var) {
+__device__ __forceinline__ unsigned rpc_key(unsigned long long seed, long long lp, int it, int var) {
   unsigned long long z = (seed ^ (static_cast<unsigned long long>(lp) << 40) ^
                           (static_cast<unsigned long long>(it) << 20) ^ static_cast<unsigned long long>(var)) +
                          0x9e3779b97f4a7c15ull;
@@ -244,6 +244,7 @@ struct TableauParams {
   uint32_t *err;
   int rule;                    // lpb_pivot_rule
   unsigned long long seed;     // LPB_PIVOT_RPC seed
+  long long lp_base;           // batch index of LP 0 of this launch (LPB_PIVOT_RPC keys)
 };
 
 struct BackwardParams {
@@ -320,8 +321,10 @@ lpb_err solve_workspace_bytes(const DeviceInfo &d, const lpb_batch *b, const lpb
                               bool basis_given, size_t *bytes);
 // Zero `ctr` (kCounters device ints) and launch every pass of a solve on `s`,
 // with scratch from `ws`.  prof_ev (3 pairs) / prof_ran (3 flags) may be null.
+// lp_base: batch index of the batch's LP 0 (a chunk of a larger batch), which
+// the random pivot rule's keys use.
 lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_batch *b,
                   const lpb_options *o, const lpb_result *r, void *ws, size_t ws_bytes, cudaStream_t s,
-                  cudaEvent_t *prof_ev, bool *prof_ran, int *kernels = nullptr);
+                  cudaEvent_t *prof_ev, bool *prof_ran, int *kernels = nullptr, long long lp_base = 0);
 
 }  // namespace lpb

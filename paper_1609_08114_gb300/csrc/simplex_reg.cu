@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
             // The random rule ranks by the upper 31 bits of the variable's key,
             // stored as the bits of a non-negative float: the arg-min compares
             // the order-preserving integer image, never the float value.
-            cv = bland ? 0.f : P.rule == LPB_PIVOT_RPC ? __uint_as_float(rpc_key(P.seed, lp, iters, nvar) >> 1) : rj;
+            cv = bland ? 0.f : P.rule == LPB_PIVOT_RPC ? __uint_as_float(rpc_key(P.seed, P.lp_base + lp, iters, nvar) >> 1) : rj;
             ck = (nvar << kIdxBits) | j;
           }
         }

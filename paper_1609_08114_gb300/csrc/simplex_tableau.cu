@@ -260,7 +260,8 @@ __device__ __forceinline__ void pivot(const Tab<T> &S_, int rows, int l, int e) 
 // visible yet).  Keys are (variable << kIdxBits) | column.
 template <typename T>
 __device__ __forceinline__ void step1_warp(const Tab<T> &S_, int orow, bool bland, T eps_d, int ecol, int evar,
-                                           T &v, int &key, int rule, unsigned long long seed, int lp, int it) {
+                                           T &v, int &key, int rule, unsigned long long seed, long long lp,
+                                           int it) {
   const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
   const T *r = S.row(orow);
   v = pos_inf<T>();
@@ -293,7 +294,7 @@ __device__ __forceinline__ void step1_warp(const Tab<T> &S_, int orow, bool blan
 // skips them (they are redundant rows left after Phase I).
 template <typename T>
 __device__ __forceinline__ int run_phase(const Tab<T> &S_, int orow, int rows, int phase, int &iters, int max_iter,
-                         T eps_p, T eps_d, int rule, unsigned long long seed, int lp) {
+                         T eps_p, T eps_d, int rule, unsigned long long seed, long long lp) {
   const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int r0, r1;
@@ -935,7 +936,7 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
         const double w0 = -double(S.at(m + 1, S.nc));
         const double ftol = sizeof(T) == 4 ? fmax(P.feas_tol * (1.0 + bmax), 1e-5 * (1.0 + w0))
                                            : P.feas_tol * (1.0 + bmax);
-        status = run_phase(S, m + 1, m + 2, 1, iters, max_iter, eps_p, eps_d, P.rule, P.seed, lp);
+        status = run_phase(S, m + 1, m + 2, 1, iters, max_iter, eps_p, eps_d, P.rule, P.seed, P.lp_base + lp);
         if (status == LPB_OPTIMAL) {
           const double w = double(S.at(m + 1, S.nc));
           if (-w > ftol) {
@@ -950,7 +951,7 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
           }
         }
       }
-      if (status == LPB_OPTIMAL) status = run_phase(S, m, m + 1, 2, iters, max_iter, eps_p, eps_d, P.rule, P.seed, lp);
+      if (status == LPB_OPTIMAL) status = run_phase(S, m, m + 1, 2, iters, max_iter, eps_p, eps_d, P.rule, P.seed, P.lp_base + lp);
     }
     if constexpr (sizeof(T) == 4) if (P.mode == MODE_FP32_REFINE) {
       bool done = false;
