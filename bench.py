@@ -7,7 +7,8 @@ refinement and KKT certificate, FP64 re-solve of failures, outputs.  Prints one 
 
 Secondary legs (skip with ``--no-legs``) time the other workloads once each with CUDA
 events: 1,000 x m=n=16; the m=n sweep; the two Step 1 rules (most negative reduced cost
-vs a random eligible column) on 50,000 x m=n=100; 10,000 x m=n=200 two-phase; hyperbox
+vs a random eligible column) on 50,000 x m=n=100; one m=n=100 polytope in 50,000
+directions (shared constraints); 10,000 x m=n=200 two-phase; hyperbox
 support functions (4,000,000 x 5 FP32, 6,000,000 x 28 FP64); 20,000 mixed sizes forward
 and forward+backward.
 
@@ -409,6 +410,22 @@ def secondary_legs(solver, dev):
     solve_leg("type1_50000x100_lpc", bt, reps=3)
     solve_leg("type1_50000x100_rpc", bt, reps=3, pivot_rule="rpc", seed=1)
     del bt
+    torch.cuda.empty_cache()
+    # support functions of one polytope (m=n=100, type-1 values) in 50,000 directions
+    # c ~ U[0,1] (lpb_solve_shared: A and b read once per LP from L2, not HBM)
+    g = torch.Generator(device=dev)
+    g.manual_seed(101)
+    A1 = 0.1 + 0.9 * torch.rand((100, 100), generator=g, device=dev, dtype=torch.float64)
+    b1 = 1 + 9 * torch.rand(100, generator=g, device=dev, dtype=torch.float64)
+    C1 = torch.rand((50_000, 100), generator=g, device=dev, dtype=torch.float64)
+    leg = {"count": 50_000, "m": 100, "n": 100}
+    for prec in ("fp32_refine", "fp64"):
+        r = solver.solve_shared(A1, b1, C1, prec=prec)
+        ms = _time(lambda: solver.solve_shared(A1, b1, C1, prec=prec, out=r), reps=3)
+        leg[prec] = {"LPs_per_s": 50_000 / (ms * 1e-3), "ms": ms, "pivots_per_lp": float(r.iters.float().mean()),
+                     "statuses": {str(k): int(v) for k, v in zip(*np.unique(r.status.cpu().numpy(), return_counts=True))}}
+    out["shared_polytope_50000x100"] = leg
+    del A1, b1, C1
     torch.cuda.empty_cache()
     # 10,000 x m=n=200 two-phase
     sb = synth.type2(10_000, 200, 200, seed=2)

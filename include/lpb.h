@@ -224,6 +224,26 @@ lpb_err lpb_workspace_size_host(lpb_handle *handle, const lpb_batch *host_batch,
 lpb_err lpb_solve_host(lpb_handle *handle, const lpb_batch *host_batch, const lpb_options *opt,
                        const lpb_result *host_result, int32_t chunk, void *ws, size_t ws_bytes, void *stream);
 
+/* Shared-constraint batches: the support function of one polytope in many
+ * directions, Section 6's application (sampling the support function of
+ * {A x <= b, x >= 0} along `count` directions).  For k < count:
+ *
+ *     maximize  C[k]^T x   subject to  A x <= b,  x >= 0,
+ *
+ * with one A (m x n row-major) and b (m) shared by every LP, C count x n
+ * row-major; A, b and C have dtype `dtype` and live on the device.  Results
+ * (device, caller-owned, FP64): status, iters, obj per direction; x of LP k at
+ * k n (count x n); y and basis (nullable) of LP k at k m (count x m).  Every
+ * LP reads the one copy of A and b, which stays in L2 across the batch; the
+ * solve is otherwise that of lpb_solve (all precisions, pivot rules, Phase I
+ * when some b_i < 0).  `ws` is device memory of lpb_workspace_size_shared()
+ * bytes, 256-byte aligned.  Asynchronous on `stream`. */
+lpb_err lpb_workspace_size_shared(lpb_handle *handle, int32_t m, int32_t n, int32_t dtype, int64_t count,
+                                  const lpb_options *opt, size_t *bytes);
+lpb_err lpb_solve_shared(lpb_handle *handle, int32_t m, int32_t n, int32_t dtype, const void *A, const void *b,
+                         int64_t count, const void *C, const lpb_options *opt, const lpb_result *result,
+                         void *ws, size_t ws_bytes, void *stream);
+
 /* lpb_solve for callers that cannot allocate device memory.  The paper has no
  * counterpart; this exists for plug-ins whose host framework owns all device
  * memory through its own pool, and for loops where cudaMalloc / cudaFree are

@@ -200,6 +200,32 @@ class Solver:
                                            _ptr(ws), ws.numel(), _stream_handle(self.device)), "lpb_solve_host")
         return res
 
+    def solve_shared(self, A: torch.Tensor, b: torch.Tensor, C: torch.Tensor, prec="fp32_refine",
+                     out: SolveResult | None = None, **kw) -> SolveResult:
+        """Support function of one polytope ``{A x <= b, x >= 0}`` in every direction of
+        ``C[count, n]`` (lpb_solve_shared): x of direction k at ``k n``, y and basis at ``k m``."""
+        m, n = A.shape
+        count = C.shape[0]
+        dt = {torch.float32: _lib.DTYPE_F32, torch.float64: _lib.DTYPE_F64}[A.dtype]
+        if b.dtype != A.dtype or C.dtype != A.dtype or C.shape[1] != n or b.numel() != m:
+            raise ValueError("A (m x n), b (m) and C (count x n) must share one dtype")
+        A, b, C = A.contiguous(), b.contiguous(), C.contiguous()
+        opt = self.options(prec, **kw)
+        dev = A.device
+        res = out if out is not None else SolveResult(
+            torch.empty(count, dtype=torch.int32, device=dev), torch.empty(count, dtype=torch.int32, device=dev),
+            torch.empty(count, dtype=torch.float64, device=dev), torch.empty(count * n, dtype=torch.float64, device=dev),
+            torch.empty(count * m, dtype=torch.float64, device=dev), torch.empty(count * m, dtype=torch.int32, device=dev))
+        nb = ctypes.c_size_t()
+        _lib.check(self.lib.lpb_workspace_size_shared(self.h, m, n, dt, count, ctypes.byref(opt), ctypes.byref(nb)),
+                   "lpb_workspace_size_shared")
+        ws = self.workspace(int(nb.value))
+        cr = res.cstruct()
+        _lib.check(self.lib.lpb_solve_shared(self.h, m, n, dt, _ptr(A), _ptr(b), count, _ptr(C), ctypes.byref(opt),
+                                             ctypes.byref(cr), _ptr(ws), ws.numel(), _stream_handle(self.device)),
+                   "lpb_solve_shared")
+        return res
+
     def autotune(self, batch: LPBatch, prec="fp32_refine", table_path: str | None = None,
                  out: SolveResult | None = None, **kw) -> float:
         """Pick the fastest schedule for batches shaped like ``batch`` (lpb_autotune); later solves

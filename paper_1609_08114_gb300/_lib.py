@@ -65,6 +65,10 @@ SIGNATURES = {
                                                ctypes.POINTER(ctypes.c_size_t)]),
     "lpb_solve_host": (ctypes.c_int, [P, ctypes.POINTER(Batch), ctypes.POINTER(Options), ctypes.POINTER(Result),
                                       ctypes.c_int32, P, ctypes.c_size_t, P]),
+    "lpb_workspace_size_shared": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                                 ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_size_t)]),
+    "lpb_solve_shared": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_int64, P,
+                                        ctypes.POINTER(Options), ctypes.POINTER(Result), P, ctypes.c_size_t, P]),
     "lpb_hyperbox": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P, P,
                                     ctypes.c_int32, P, P, P]),
     "lpb_autotune": (ctypes.c_int, [P, ctypes.POINTER(Batch), ctypes.POINTER(Options), ctypes.POINTER(Result), P,

@@ -289,7 +289,7 @@ TableauParams base_params(int32_t *ctr, uint32_t *err, const lpb_batch *b, const
   TableauParams p{};
   p.B = BatchDev{b->count, b->max_m, b->max_n, b->dtype, b->m, b->n, b->a_off, b->b_off, b->c_off,
                  b->A, b->b, b->c};
-  p.R = ResultDev{r->status, r->iters, r->obj, r->x, r->y, r->basis};
+  p.R = ResultDev{r->status, r->iters, r->obj, r->x, r->y, r->basis, nullptr};
   p.defer_items = reinterpret_cast<int32_t *>(ws + pl.off_defer);
   p.defer_count = ctr + CTR_DEFER;
   p.resolve_items = reinterpret_cast<int32_t *>(ws + pl.off_resolve);
@@ -325,7 +325,7 @@ lpb_err solve_workspace_bytes(const DeviceInfo &d, const lpb_batch *b, const lpb
 
 lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_batch *b,
                   const lpb_options *o, const lpb_result *r, void *ws, size_t ws_bytes, cudaStream_t s,
-                  cudaEvent_t *prof_ev, bool *prof_ran, int *kernels, long long lp_base) {
+                  cudaEvent_t *prof_ev, bool *prof_ran, int *kernels, long long lp_base, const int64_t *y_off) {
   if (kernels) *kernels = 0;
   Plan pl;
   lpb_err e = make_plan(d, b, o, r->basis != nullptr, &pl);
@@ -363,6 +363,7 @@ lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_ba
     }
     TableauParams p = base_params(ctr, err, b, r, o, pl, w);
     p.lp_base = lp_base;
+    p.R.y_off = y_off;
     p.kcap = ps.kcap;
     p.mode = ps.mode;
     p.slot_bytes = ps.slot_bytes;
@@ -482,6 +483,54 @@ lpb_err make_host_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_option
   hp->o_bs = take(hp->b_max * 4);
   hp->set_bytes = off;
   hp->total = align256(hp->solve_ws) + 2 * hp->set_bytes;
+  return LPB_OK;
+}
+
+}  // namespace
+
+// ---- shared-constraint batches: one A and b, many objectives ----------------
+
+namespace {
+
+// Sizes and offsets of `count` LPs that share A and b (offset 0) and read
+// objective k at k n; y and basis of LP k go to k m of the result.
+__global__ void fill_shared_meta(int32_t *m, int32_t *n, int64_t *a_off, int64_t *b_off, int64_t *c_off,
+                                 int64_t *y_off, int count, int mm, int nn) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+    m[k] = mm;
+    n[k] = nn;
+    a_off[k] = 0;
+    b_off[k] = 0;
+    c_off[k] = int64_t(k) * nn;
+    y_off[k] = int64_t(k) * mm;
+  }
+}
+
+struct SharedPlan {
+  size_t o_m = 0, o_n = 0, o_ao = 0, o_bo = 0, o_co = 0, o_yo = 0, o_ws = 0, solve_ws = 0, total = 0;
+};
+
+lpb_err make_shared_plan(const DeviceInfo &d, int m, int n, int dtype, int64_t count, const lpb_options *o,
+                         SharedPlan *sp) {
+  if (!o || m < 1 || n < 1 || count < 0 || count > INT32_MAX) return LPB_EINVAL;
+  lpb_batch pb{};
+  pb.count = int32_t(count);
+  pb.max_m = m;
+  pb.max_n = n;
+  pb.dtype = dtype;
+  const lpb_err e = solve_workspace_bytes(d, &pb, o, false, &sp->solve_ws);
+  if (e != LPB_OK) return e;
+  const size_t c = size_t(count > 0 ? count : 1);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t at = off; off = align256(off + bytes); return at; };
+  sp->o_m = take(c * 4);
+  sp->o_n = take(c * 4);
+  sp->o_ao = take(c * 8);
+  sp->o_bo = take(c * 8);
+  sp->o_co = take(c * 8);
+  sp->o_yo = take(c * 8);
+  sp->o_ws = take(sp->solve_ws);
+  sp->total = off;
   return LPB_OK;
 }
 
@@ -721,6 +770,59 @@ lpb_err lpb_solve_host(lpb_handle *h, const lpb_batch *b, const lpb_options *o, 
   for (int j = 0; j < 2 && j < hp.nchunk; ++j)
     if (!ok(cudaStreamWaitEvent(s, h->ev_out[j], 0))) return LPB_ECUDA;
   return LPB_OK;
+}
+
+lpb_err lpb_workspace_size_shared(lpb_handle *h, int32_t m, int32_t n, int32_t dtype, int64_t count,
+                                  const lpb_options *o, size_t *bytes) {
+  if (!h || !o || !bytes) return LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  SharedPlan sp;
+  const lpb_err e = make_shared_plan(device_info(h), m, n, dtype, count, o, &sp);
+  if (e != LPB_OK) return e;
+  *bytes = sp.total;
+  return LPB_OK;
+}
+
+lpb_err lpb_solve_shared(lpb_handle *h, int32_t m, int32_t n, int32_t dtype, const void *A, const void *b,
+                         int64_t count, const void *C, const lpb_options *o, const lpb_result *r, void *ws,
+                         size_t ws_bytes, void *stream) {
+  if (!h || !o || !r) return LPB_EINVAL;
+  if (count == 0) return LPB_OK;
+  if (!A || !b || !C || !r->status || !r->obj || !r->x) return LPB_EINVAL;
+  if (dtype != LPB_DTYPE_F32 && dtype != LPB_DTYPE_F64) return LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  const DeviceInfo d = device_info(h);
+  SharedPlan sp;
+  lpb_err e = make_shared_plan(d, m, n, dtype, count, o, &sp);
+  if (e != LPB_OK) return e;
+  if (ws_bytes < sp.total || !ws) return LPB_ENOMEM;
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return LPB_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char *w = static_cast<unsigned char *>(ws);
+  int32_t *dm = reinterpret_cast<int32_t *>(w + sp.o_m), *dn = reinterpret_cast<int32_t *>(w + sp.o_n);
+  int64_t *dao = reinterpret_cast<int64_t *>(w + sp.o_ao), *dbo = reinterpret_cast<int64_t *>(w + sp.o_bo);
+  int64_t *dco = reinterpret_cast<int64_t *>(w + sp.o_co), *dyo = reinterpret_cast<int64_t *>(w + sp.o_yo);
+  const int cnt = int(count);
+  const int grid = (cnt + 255) / 256 < 4 * d.sms ? (cnt + 255) / 256 : 4 * d.sms;
+  fill_shared_meta<<<grid, 256, 0, s>>>(dm, dn, dao, dbo, dco, dyo, cnt, m, n);
+  if (cudaGetLastError() != cudaSuccess) return LPB_ECUDA;
+  lpb_batch bt{};
+  bt.count = cnt;
+  bt.max_m = m;
+  bt.max_n = n;
+  bt.dtype = dtype;
+  bt.m = dm;
+  bt.n = dn;
+  bt.a_off = dao;
+  bt.b_off = dbo;
+  bt.c_off = dco;
+  bt.A = A;
+  bt.b = b;
+  bt.c = C;
+  return run_solve(d, h->d_ctr, h->d_err, &bt, o, r, w + sp.o_ws, sp.solve_ws, s, nullptr, nullptr,
+                   &h->last_kernels, 0, dyo);
 }
 
 lpb_err lpb_autotune(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const lpb_result *r,

@@ -40,6 +40,7 @@ struct ResultDev {
   int32_t *status, *iters;
   double *obj, *x, *y;
   int32_t *basis;
+  const int64_t *y_off;   // where y and basis of LP k start; null: at b_off[k] (packed like b)
 };
 
 // A list of LP indices with a device-resident length.  `items == nullptr`
@@ -322,9 +323,11 @@ lpb_err solve_workspace_bytes(const DeviceInfo &d, const lpb_batch *b, const lpb
 // Zero `ctr` (kCounters device ints) and launch every pass of a solve on `s`,
 // with scratch from `ws`.  prof_ev (3 pairs) / prof_ran (3 flags) may be null.
 // lp_base: batch index of the batch's LP 0 (a chunk of a larger batch), which
-// the random pivot rule's keys use.
+// the random pivot rule's keys use.  y_off (device, nullable): where y and the
+// basis of LP k go in the result (default: b_off[k]).
 lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_batch *b,
                   const lpb_options *o, const lpb_result *r, void *ws, size_t ws_bytes, cudaStream_t s,
-                  cudaEvent_t *prof_ev, bool *prof_ran, int *kernels = nullptr, long long lp_base = 0);
+                  cudaEvent_t *prof_ev, bool *prof_ran, int *kernels = nullptr, long long lp_base = 0,
+                  const int64_t *y_off = nullptr);
 
 }  // namespace lpb

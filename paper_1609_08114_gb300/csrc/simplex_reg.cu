@@ -596,11 +596,12 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     if (lane < C) sh.nonb[wid + W * lane] = nvar;
     __syncthreads();
 
-    int32_t *bp = P.bbuf ? P.bbuf + (P.bpacked ? boff : int64_t(lp) * P.B.max_m) : nullptr;
+    const int64_t yoff = P.R.y_off ? P.R.y_off[lp] : boff;    // outputs packed like b, or at y_off
+    int32_t *bp = P.bbuf ? P.bbuf + (P.bpacked ? yoff : int64_t(lp) * P.B.max_m) : nullptr;
     if (status != LPB_OPTIMAL || P.mode != MODE_FP32_REFINE) {
       if (status == LPB_OPTIMAL) {   // plain FP32: results straight from the tableau
         for (int j = tid; j < n; j += NT) P.R.x[coff + j] = 0.0;
-        if (P.R.y) for (int i = tid; i < m; i += NT) P.R.y[boff + i] = 0.0;
+        if (P.R.y) for (int i = tid; i < m; i += NT) P.R.y[yoff + i] = 0.0;
         __syncthreads();
         for (int i = tid; i < m; i += NT)
           if (sh.basic[i] < n) P.R.x[coff + sh.basic[i]] = double(sh.rhs[i]);
@@ -609,7 +610,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
           for (int c = 0; c < C; ++c) {
             if (wid == W - 1 && c == C - 1) continue;    // the right-hand side
             const int v = sh.nonb[wid + W * c];
-            if (v >= n && v < n + m) P.R.y[boff + (v - n)] = double(T[R - 1][c]);
+            if (v >= n && v < n + m) P.R.y[yoff + (v - n)] = double(T[R - 1][c]);
           }
         }
         if (wid == W - 1 && lane == 31) {
@@ -625,7 +626,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
         }
       } else {                                   // plain FP32: final as found
         for (int j = tid; j < n; j += NT) P.R.x[coff + j] = 0.0;
-        if (P.R.y) for (int i = tid; i < m; i += NT) P.R.y[boff + i] = 0.0;
+        if (P.R.y) for (int i = tid; i < m; i += NT) P.R.y[yoff + i] = 0.0;
         if (tid == 0) {
           P.R.status[lp] = status;
           if (P.R.iters) P.R.iters[lp] = iters;
@@ -893,7 +894,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     if (bp) for (int i = tid; i < m; i += NT) bp[i] = sh.basic[i];
     if (!fail) {
       for (int j = tid; j < n; j += NT) P.R.x[coff + j] = sh.posx[j] >= 0 ? sh.xb[sh.posx[j]] : 0.0;
-      if (P.R.y) for (int k = tid; k < m; k += NT) P.R.y[boff + k] = sh.yv[k];
+      if (P.R.y) for (int k = tid; k < m; k += NT) P.R.y[yoff + k] = sh.yv[k];
     }
     if (tid == 0) {
       const double cx = sh.red[0][0];

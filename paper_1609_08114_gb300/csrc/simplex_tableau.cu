@@ -627,19 +627,19 @@ __device__ __forceinline__ bool dual_cleanup(const Tab<T> &S_, int rows, int &it
 }
 
 // Write the FP64 outputs of LP `lp` from the tableau (FP64 and plain FP32 modes).
-__device__ __forceinline__ int32_t *basis_at(const TableauParams &P, int lp, int64_t boff) {
-  return P.bbuf ? P.bbuf + (P.bpacked ? boff : int64_t(lp) * P.B.max_m) : nullptr;
+__device__ __forceinline__ int32_t *basis_at(const TableauParams &P, int lp, int64_t yoff) {
+  return P.bbuf ? P.bbuf + (P.bpacked ? yoff : int64_t(lp) * P.B.max_m) : nullptr;
 }
 
 template <typename T>
 __device__ __forceinline__ void write_from_tableau(const Tab<T> &S_, const ResultDev &R_, int32_t *basis, int lp,
-                                   int64_t boff, int64_t coff, int status, int iters) {
+                                   int64_t yoff, int64_t coff, int status, int iters) {
   const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
   const ResultDev R = R_;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int m = S.m, n = S.n;
   for (int j = tid; j < n; j += nt) R.x[coff + j] = 0.0;
-  if (R.y) for (int i = tid; i < m; i += nt) R.y[boff + i] = 0.0;
+  if (R.y) for (int i = tid; i < m; i += nt) R.y[yoff + i] = 0.0;
   __syncthreads();
   if (status == LPB_OPTIMAL) {
     for (int i = tid; i < m; i += nt) {
@@ -649,7 +649,7 @@ __device__ __forceinline__ void write_from_tableau(const Tab<T> &S_, const Resul
     if (R.y)
       for (int j = tid; j < S.nc; j += nt) {
         const int v = S.nonb[j];
-        if (v >= n && v < n + m) R.y[boff + (v - n)] = double(S.at(m, j));
+        if (v >= n && v < n + m) R.y[yoff + (v - n)] = double(S.at(m, j));
       }
   }
   if (basis)
@@ -667,8 +667,8 @@ __device__ __forceinline__ void write_from_tableau(const Tab<T> &S_, const Resul
 // writes the outputs when the refined pair (x, y) passes the checks.
 __device__ __forceinline__ bool refine_and_verify(const Tab<float> &S_, const BatchDev &B_, const ResultDev &R_,
                                                   int32_t *basis, const Layout &L, unsigned char *smem, int lp,
-                                                  int64_t aoff, int64_t boff, int64_t coff, int iters, double tol,
-                                                  double bmax, double cmax) {
+                                                  int64_t aoff, int64_t boff, int64_t coff, int64_t yoff, int iters,
+                                                  double tol, double bmax, double cmax) {
   const Tab<float> S = S_;   // a register copy: stores through tableau pointers cannot alias it
   const BatchDev B = B_;
   const ResultDev R = R_;
@@ -816,7 +816,7 @@ __device__ __forceinline__ bool refine_and_verify(const Tab<float> &S_, const Ba
   for (int j = tid; j < n; j += nt) R.x[coff + j] = 0.0;
   __syncthreads();
   for (int q = tid; q < nsb; q += nt) R.x[coff + jq[q]] = xb[sb[q]];
-  if (R.y) for (int k = tid; k < m; k += nt) R.y[boff + k] = yv[k];
+  if (R.y) for (int k = tid; k < m; k += nt) R.y[yoff + k] = yv[k];
   if (basis) for (int i = tid; i < m; i += nt) basis[i] = S.basic[i];
   if (tid == 0) {
     R.status[lp] = LPB_OPTIMAL;
@@ -869,6 +869,7 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
       continue;
     }
     const int64_t aoff = P.B.a_off[lp], boff = P.B.b_off[lp], coff = P.B.c_off[lp];
+    const int64_t yoff = P.R.y_off ? P.R.y_off[lp] : boff;    // outputs packed like b, or at y_off
     // Negated rows, |b|max and |c|max.
     if (tid == 0) { s_k = 0; s_bmax = 0ull; s_cmax = 0ull; }
     __syncthreads();
@@ -919,8 +920,8 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
       status = LPB_NUMERIC;
     } else {
       bool warm = false;
-      if (P.warm && basis_at(P, lp, boff)) {
-        warm = warm_start(S, basis_at(P, lp, boff), iters, eps_p) &&
+      if (P.warm && basis_at(P, lp, yoff)) {
+        warm = warm_start(S, basis_at(P, lp, yoff), iters, eps_p) &&
                dual_cleanup(S, m + (S.k ? 2 : 1), iters, max_iter, eps_p);
         if (!warm) {         // cold restart
           iters = 0;
@@ -959,11 +960,11 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
         int dropped = 0;
         for (int i = tid; i < m; i += nt) dropped |= S.basic[i] >= S.nm;
         if (!__syncthreads_or(dropped))
-          done = refine_and_verify(S, P.B, P.R, basis_at(P, lp, boff), L, smem, lp, aoff, boff,
-                                   coff, iters, P.feas_tol, bmax, cmax);
+          done = refine_and_verify(S, P.B, P.R, basis_at(P, lp, yoff), L, smem, lp, aoff, boff,
+                                   coff, yoff, iters, P.feas_tol, bmax, cmax);
       }
       if (!done) {
-        if (int32_t *bp = basis_at(P, lp, boff))
+        if (int32_t *bp = basis_at(P, lp, yoff))
           for (int i = tid; i < m; i += nt) bp[i] = S.basic[i] < S.nm ? S.basic[i] : -1;
         if (tid == 0) {
           P.R.status[lp] = STATUS_PENDING;
@@ -974,7 +975,7 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
       __syncthreads();
       continue;
     }
-    write_from_tableau(S, P.R, basis_at(P, lp, boff), lp, boff, coff, status, iters);
+    write_from_tableau(S, P.R, basis_at(P, lp, yoff), lp, yoff, coff, status, iters);
     __syncthreads();
   }
 }
