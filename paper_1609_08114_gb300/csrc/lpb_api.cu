@@ -325,7 +325,8 @@ lpb_err solve_workspace_bytes(const DeviceInfo &d, const lpb_batch *b, const lpb
 
 lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_batch *b,
                   const lpb_options *o, const lpb_result *r, void *ws, size_t ws_bytes, cudaStream_t s,
-                  cudaEvent_t *prof_ev, bool *prof_ran, int *kernels, long long lp_base, const int64_t *y_off) {
+                  cudaEvent_t *prof_ev, bool *prof_ran, int *kernels, long long lp_base, const int64_t *y_off,
+                  int shared) {
   if (kernels) *kernels = 0;
   Plan pl;
   lpb_err e = make_plan(d, b, o, r->basis != nullptr, &pl);
@@ -364,6 +365,7 @@ lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_ba
     TableauParams p = base_params(ctr, err, b, r, o, pl, w);
     p.lp_base = lp_base;
     p.R.y_off = y_off;
+    p.shared = shared;
     p.kcap = ps.kcap;
     p.mode = ps.mode;
     p.slot_bytes = ps.slot_bytes;
@@ -504,6 +506,18 @@ __global__ void fill_shared_meta(int32_t *m, int32_t *n, int64_t *a_off, int64_t
     c_off[k] = int64_t(k) * nn;
     y_off[k] = int64_t(k) * mm;
   }
+}
+
+// Options of a shared-constraint solve: FP32 solves that fit a register
+// template run on the register kernel over the identity work list, so that
+// each CTA takes consecutive objectives and can start each from the basis of
+// the one before.
+lpb_options shared_options(const lpb_options *o, int m, int n) {
+  lpb_options os = *o;
+  if (o->prec != LPB_FP64 && o->kernel == LPB_KERNEL_AUTO && o->threads == 0 &&
+      reg_pick(m, n, o->reg_warps > 0 ? o->reg_warps : 8) >= 0)
+    os.kernel = LPB_KERNEL_REG;
+  return os;
 }
 
 struct SharedPlan {
@@ -778,7 +792,8 @@ lpb_err lpb_workspace_size_shared(lpb_handle *h, int32_t m, int32_t n, int32_t d
   DeviceScope ds(h->device);
   if (!ds.ok()) return LPB_ECUDA;
   SharedPlan sp;
-  const lpb_err e = make_shared_plan(device_info(h), m, n, dtype, count, o, &sp);
+  const lpb_options os = shared_options(o, m, n);
+  const lpb_err e = make_shared_plan(device_info(h), m, n, dtype, count, &os, &sp);
   if (e != LPB_OK) return e;
   *bytes = sp.total;
   return LPB_OK;
@@ -795,6 +810,8 @@ lpb_err lpb_solve_shared(lpb_handle *h, int32_t m, int32_t n, int32_t dtype, con
   if (!ds.ok()) return LPB_ECUDA;
   const DeviceInfo d = device_info(h);
   SharedPlan sp;
+  const lpb_options os = shared_options(o, m, n);
+  o = &os;
   lpb_err e = make_shared_plan(d, m, n, dtype, count, o, &sp);
   if (e != LPB_OK) return e;
   if (ws_bytes < sp.total || !ws) return LPB_ENOMEM;
@@ -822,7 +839,7 @@ lpb_err lpb_solve_shared(lpb_handle *h, int32_t m, int32_t n, int32_t dtype, con
   bt.b = b;
   bt.c = C;
   return run_solve(d, h->d_ctr, h->d_err, &bt, o, r, w + sp.o_ws, sp.solve_ws, s, nullptr, nullptr,
-                   &h->last_kernels, 0, dyo);
+                   &h->last_kernels, 0, dyo, 1);
 }
 
 lpb_err lpb_autotune(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const lpb_result *r,

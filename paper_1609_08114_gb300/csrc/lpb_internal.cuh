@@ -246,6 +246,7 @@ struct TableauParams {
   int rule;                    // lpb_pivot_rule
   unsigned long long seed;     // LPB_PIVOT_RPC seed
   long long lp_base;           // batch index of LP 0 of this launch (LPB_PIVOT_RPC keys)
+  int shared;                  // every LP shares A and b (lpb_solve_shared): warm starts
 };
 
 struct BackwardParams {
@@ -324,10 +325,12 @@ lpb_err solve_workspace_bytes(const DeviceInfo &d, const lpb_batch *b, const lpb
 // with scratch from `ws`.  prof_ev (3 pairs) / prof_ran (3 flags) may be null.
 // lp_base: batch index of the batch's LP 0 (a chunk of a larger batch), which
 // the random pivot rule's keys use.  y_off (device, nullable): where y and the
-// basis of LP k go in the result (default: b_off[k]).
+// basis of LP k go in the result (default: b_off[k]).  shared: every LP reads
+// the same A and b, so the register kernel may start an LP from the basis of
+// the one it solved before.
 lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_batch *b,
                   const lpb_options *o, const lpb_result *r, void *ws, size_t ws_bytes, cudaStream_t s,
                   cudaEvent_t *prof_ev, bool *prof_ran, int *kernels = nullptr, long long lp_base = 0,
-                  const int64_t *y_off = nullptr);
+                  const int64_t *y_off = nullptr, int shared = 0);
 
 }  // namespace lpb

@@ -73,6 +73,11 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 constexpr int kBad = 1 << 30;   // a key larger than any real key
+// Shared-constraint batches: consecutive objectives claimed at a time, and
+// warm starts between two cold builds of the tableau (FP32 round-off grows
+// with the pivots a tableau has been through).
+constexpr int kShareChunk = 16;
+constexpr int kWarmMax = 32;
 
 // Bulk prefetch of [p, p + bytes) into L2, shrunk to whole 16-byte units
 // inside the range; a hint with no completion to wait for.
@@ -120,6 +125,7 @@ struct RegShared {
   int nonb[COLS];
   alignas(16) float objv[W][(C + 3) & ~3];   // objective row, per warp
   int item, nsb, nns;
+  int warm_ok;                               // shared constraints: start from the previous basis
   unsigned long long bmax, cmax;
   uint64_t abar;                             // completion of the bulk copies of A
   double xb[ROWS], rr[ROWS], yv[ROWS], sax[ROWS], dj[COLS];
@@ -260,13 +266,37 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
   // Lane 0 of the last warp claims work items one LP ahead, so that the next
   // LP's data can be prefetched into L2 while this one is solved.
   const int claimer = NT - 32;
+  // A shared-constraint batch (one A and b, many objectives) is claimed in
+  // chunks of consecutive objectives, so that a CTA starts each objective from
+  // the optimal basis of the one before (the tableau stays in registers).
+  auto claim = [&](int cur) -> int {
+    if (P.shared) {
+      if (cur >= 0 && (cur + 1) % kShareChunk != 0 && cur + 1 < nitems) return cur + 1;
+      return atomicAdd(P.queue, 1) * kShareChunk;
+    }
+    return atomicAdd(P.queue, 1);
+  };
   int next = 0;
-  if (tid == claimer) next = atomicAdd(P.queue, 1);
+  if (tid == claimer) next = claim(-1);
+  // The basis of the last tableau: every lane keeps, for its rows lane + 32 r,
+  // the basic variable and the right-hand side (the same FP32 values warp W-1
+  // holds in its last column); lane c < C keeps the variable of the warp's
+  // column wid + W c.  valid_tab: the registers hold a basis tableau of this
+  // batch's A and b; warm_run: objectives solved since the last cold start.
+  int bvar[R];
+  float rhsr[R];
+  int nvar = kBad >> kIdxBits;
+  int valid_tab = 0, warm_run = 0;
+  int sld_res = sld_pad;                       // row stride of the resident A
   for (;;) {
     if (tid == claimer) sh.item = next;
+    if (tid == 0) sh.warm_ok = P.shared && valid_tab && warm_run < kWarmMax;
     __syncthreads();
     const int item = sh.item;
     if (item >= nitems) break;
+    const bool warm = sh.warm_ok != 0;     // keep the basis; load and price only the new objective
+    warm_run = warm ? warm_run + 1 : 0;
+    valid_tab = 0;
     const int lp = P.in.items ? P.in.items[item] : item;
     const int m = P.B.m[lp], n = P.B.n[lp];
     const int64_t aoff = P.B.a_off[lp], boff = P.B.b_off[lp], coff = P.B.c_off[lp];
@@ -283,36 +313,40 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     // of more bank conflicts in the column reads); else rows whose start and
     // length are whole 16-byte units go by one bulk copy each into rows of a
     // padded stride, and the rest by 4- or 8-byte asynchronous copies.
-    const bool dense = fits && ((reinterpret_cast<uintptr_t>(Ag) | uintptr_t(m) * uintptr_t(n) * es) & 15) == 0;
-    const bool bulk = fits && !dense && ((reinterpret_cast<uintptr_t>(Ag) | uintptr_t(n) * es) & 15) == 0;
-    const int sld = dense ? n : sld_pad;
+    const bool dense = fits && !warm && ((reinterpret_cast<uintptr_t>(Ag) | uintptr_t(m) * uintptr_t(n) * es) & 15) == 0;
+    const bool bulk = fits && !warm && !dense && ((reinterpret_cast<uintptr_t>(Ag) | uintptr_t(n) * es) & 15) == 0;
+    if (!warm) sld_res = dense ? n : sld_pad;   // a warm start reuses the resident A in its layout
+    const int sld = sld_res;
     // b and c go by bulk copy on the same barrier as A when their starts and
     // lengths are whole 16-byte units, so that one wait covers all three.
     const unsigned char *bgp = static_cast<const unsigned char *>(P.B.b) + boff * es;
     const unsigned char *cgp = static_cast<const unsigned char *>(P.B.c) + coff * es;
-    const bool bulk_bc = fits && ((reinterpret_cast<uintptr_t>(bgp) | reinterpret_cast<uintptr_t>(cgp) |
-                                   uintptr_t(m) * es | uintptr_t(n) * es) & 15) == 0;
+    const bool bulk_bc = fits && !warm && ((reinterpret_cast<uintptr_t>(bgp) | reinterpret_cast<uintptr_t>(cgp) |
+                                            uintptr_t(m) * es | uintptr_t(n) * es) & 15) == 0;
+    const bool bulk_c = fits && warm && ((reinterpret_cast<uintptr_t>(cgp) | uintptr_t(n) * es) & 15) == 0;
     if (fits) {
-      if (!bulk_bc) {
+      if (!bulk_bc && !bulk_c) {      // b (not on a warm start, it is resident) and c by small copies
         if (dt == LPB_DTYPE_F64) {
           const double *bg = reinterpret_cast<const double *>(bgp), *cg = reinterpret_cast<const double *>(cgp);
-          for (int i = tid; i < m; i += NT) cp_async8(sh.bin + i, bg + i);
+          for (int i = tid; i < (warm ? 0 : m); i += NT) cp_async8(sh.bin + i, bg + i);
           for (int j = tid; j < n; j += NT) cp_async8(sh.cin + j, cg + j);
         } else {
           const float *bg = reinterpret_cast<const float *>(bgp), *cg = reinterpret_cast<const float *>(cgp);
-          for (int i = tid; i < m; i += NT) cp_async4(reinterpret_cast<float *>(sh.bin) + i, bg + i);
+          for (int i = tid; i < (warm ? 0 : m); i += NT) cp_async4(reinterpret_cast<float *>(sh.bin) + i, bg + i);
           for (int j = tid; j < n; j += NT) cp_async4(reinterpret_cast<float *>(sh.cin) + j, cg + j);
         }
       }
-      if (dense || bulk || bulk_bc) {
+      if (dense || bulk || bulk_bc || bulk_c) {
         if (wid == 0) {
           if (lane == 0) {
             mbar_expect_tx(&sh.abar, (dense || bulk ? unsigned(m) * unsigned(n) * unsigned(es) : 0u) +
-                                         (bulk_bc ? unsigned(m + n) * unsigned(es) : 0u));
+                                         (bulk_bc ? unsigned(m + n) * unsigned(es) : 0u) +
+                                         (bulk_c ? unsigned(n) * unsigned(es) : 0u));
             if (bulk_bc) {
               bulk_load(sh.bin, bgp, unsigned(m) * es, &sh.abar);
               bulk_load(sh.cin, cgp, unsigned(n) * es, &sh.abar);
             }
+            if (bulk_c) bulk_load(sh.cin, cgp, unsigned(n) * es, &sh.abar);
             if (dense) bulk_load(sA, Ag, unsigned(m) * unsigned(n) * es, &sh.abar);
           }
           __syncwarp();
@@ -321,7 +355,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
               bulk_load(sA + size_t(i) * sld * es, Ag + size_t(i) * n * es, unsigned(n) * es, &sh.abar);
         }
       }
-      if (!bulk && !dense) {
+      if (!bulk && !dense && !warm) {
         if (dt == LPB_DTYPE_F64) {
           const double *A = reinterpret_cast<const double *>(Ag);
           double *sa = reinterpret_cast<double *>(sA);
@@ -336,14 +370,17 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       }
     }
     if (tid == claimer) {
-      next = atomicAdd(P.queue, 1);
-      if (next < nitems) prefetch_lp(P, next);
+      next = claim(item);
+      if (next < nitems && !P.shared) prefetch_lp(P, next);
     }
     int neg = 0;
-    if (tid == 0) { sh.bmax = 0ull; sh.cmax = 0ull; }
+    if (tid == 0) {
+      if (!warm) sh.bmax = 0ull;          // a warm start keeps b and its |b|max
+      sh.cmax = 0ull;
+    }
     cp_async_wait_all();
     int timed_out = 0;
-    if (dense || bulk || bulk_bc) {
+    if (dense || bulk || bulk_bc || bulk_c) {
       timed_out = !mbar_wait_bounded(&sh.abar, aphase);
       aphase ^= 1u;
     }
@@ -371,7 +408,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       // non-finite c_j send the LP elsewhere.
       constexpr unsigned long long kMag = 0x7fffffffffffffffull, kInf = 0x7ff0000000000000ull;
       unsigned long long bm = 0ull, cm = 0ull;
-      for (int i = tid; i < m; i += NT) {
+      for (int i = tid; i < (warm ? 0 : m); i += NT) {
         const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(vin(sh.bin, i, dt)));
         const unsigned long long a = u & kMag;
         neg |= int((u >> 63) != 0ull && a != 0ull) | int(a > kInf);
@@ -400,6 +437,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
 
     // ---- the tableau: A rounded to FP32, b in column COLS-1, -c in row ROWS-1 ----
     int bad = 0;
+    if (!warm) {
     if (dt == LPB_DTYPE_F64) {
       const double *sa = reinterpret_cast<const double *>(sA);
       unsigned amax = 0u;
@@ -427,18 +465,13 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
         }
       }
     }
-    // Every lane keeps, for its rows lane + 32 r, the basic variable and the
-    // right-hand side (the same FP32 values warp W-1 holds in its last
-    // column); lane c < C keeps the variable of the warp's column wid + W c.
-    int bvar[R];
-    float rhsr[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int i = lane + 32 * r;
       rhsr[r] = i < m ? vin_tile(sh.bin, i, dt, bad) : 0.f;
       bvar[r] = i < m ? n + i : kBad >> kIdxBits;
     }
-    int nvar = (wid + W * lane < n && lane < C) ? wid + W * lane : kBad >> kIdxBits;
+    nvar = (wid + W * lane < n && lane < C) ? wid + W * lane : kBad >> kIdxBits;
     if (wid == W - 1) {
 #pragma unroll
       for (int r = 0; r < R; ++r) T[r][C - 1] = rhsr[r];
@@ -450,6 +483,40 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
         if (j < n) T[R - 1][c] = -vin_tile(sh.cin, j, dt, bad);
       }
     }
+    } else {
+      // Warm start: the basis of the previous objective.  Its objective row for
+      // this c is r_j = sum_i c_B(i) t_ij - c_j on the non-basic columns and
+      // z = sum_i c_B(i) rhs_i on the right-hand side (c of slacks is 0).
+      constexpr int CP = pow2_at_least(C);
+      float cb[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) cb[r] = bvar[r] < n ? vin_tile(sh.cin, bvar[r], dt, bad) : 0.f;
+      float col[CP];
+#pragma unroll
+      for (int c = 0; c < CP; ++c) {
+        float acc = 0.f;
+        if (c < C) {
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc = fmaf(cb[r], T[r][c], acc);
+        }
+        col[c] = acc;
+      }
+      const float tot = reduce_scatter<CP>(col, lane);   // lane l: column l / (32 / CP)
+      float *objw = sh.objv[wid];
+      if (lane % (32 / CP) == 0 && lane / (32 / CP) < C) objw[lane / (32 / CP)] = tot;
+      __syncwarp();
+      if (lane < C) {
+        const bool rhs_col = wid == W - 1 && lane == C - 1;
+        const float cj = !rhs_col && nvar < n ? vin_tile(sh.cin, nvar, dt, bad) : 0.f;
+        objw[lane] -= cj;
+      }
+      __syncwarp();
+      if (lane == 31) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) T[R - 1][c] = objw[c];
+      }
+      __syncwarp();
+    }
     bad = __syncthreads_or(bad);
     if (bad) {
       if (tid == 0) {
@@ -459,6 +526,8 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       __syncthreads();
       continue;
     }
+
+    valid_tab = 1;
 
     // ---- Steps 1-3, one block barrier per pivot ----
     // Each warp takes its own best entering column (Step 1 over its columns)
@@ -584,6 +653,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
         bland = false;
       }
     }
+    valid_tab = status == LPB_OPTIMAL || status == LPB_UNBOUNDED;   // a basis tableau to start from
     // The final basis and right-hand side back to shared memory (every warp
     // holds the same copy of the rows; warp 0 writes them).
     if (wid == 0) {
@@ -891,6 +961,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       if (!fail || round == 2) break;
       __syncthreads();       // sh.red and the check inputs are rewritten by the next round
     }
+    if (fail) valid_tab = 0;            // the next objective starts cold
     if (bp) for (int i = tid; i < m; i += NT) bp[i] = sh.basic[i];
     if (!fail) {
       for (int j = tid; j < n; j += NT) P.R.x[coff + j] = sh.posx[j] >= 0 ? sh.xb[sh.posx[j]] : 0.0;

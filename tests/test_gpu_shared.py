@@ -77,16 +77,45 @@ def test_shared_unbounded_and_infeasible_regions(solver):
 
 
 def test_shared_matches_an_explicit_batch(solver):
-    """The same LPs written out as an ordinary packed batch give the same results."""
+    """The same LPs written out as an ordinary packed batch: identical results in FP64;
+    in FP32 with refinement the warm starts may end at another optimal basis, so the
+    statuses must match and the objectives agree to 1e-8."""
     from paper_1609_08114_gb300 import LPBatch
     lp = synth.type1(1, 60, 50, seed=9)
     A, b, _ = lp.lp(0)
     C = np.random.default_rng(9).uniform(0, 1, size=(256, 50))
-    res = solver.solve_shared(torch.tensor(A, device="cuda"), torch.tensor(b, device="cuda"),
-                              torch.tensor(C, device="cuda"), prec="fp32_refine")
     sb = synth.pack([(A, b, C[k]) for k in range(256)])
     batch = LPBatch.from_packed(sb.m, sb.n, sb.A, sb.b, sb.c, device="cuda")
-    ref = solver.solve(batch, prec="fp32_refine")
+    args = (torch.tensor(A, device="cuda"), torch.tensor(b, device="cuda"), torch.tensor(C, device="cuda"))
+    res = solver.solve_shared(*args, prec="fp64")
+    ref = solver.solve(batch, prec="fp64")
     torch.cuda.synchronize()
     assert torch.equal(res.status, ref.status) and torch.equal(res.obj, ref.obj) and torch.equal(res.x, ref.x)
     assert torch.equal(res.y, ref.y)
+    res = solver.solve_shared(*args, prec="fp32_refine")
+    ref = solver.solve(batch, prec="fp32_refine")
+    torch.cuda.synchronize()
+    assert torch.equal(res.status, ref.status)
+    rel = ((res.obj - ref.obj).abs() / (1 + ref.obj.abs())).max().item()
+    assert rel <= 1e-8
+
+
+def test_shared_warm_starts_cut_pivots(solver):
+    """Slowly turning directions: each objective starts from its neighbour's optimal basis,
+    so the pivots per objective fall far below a cold start's, with the same optima."""
+    lp = synth.type1(1, 80, 80, seed=12)
+    A, b, _ = lp.lp(0)
+    rng = np.random.default_rng(12)
+    c0, d = rng.uniform(0, 1, size=80), rng.normal(size=80)
+    C = c0[None, :] + 1e-3 * np.arange(2048)[:, None] * d[None, :]
+    args = (torch.tensor(A, device="cuda"), torch.tensor(b, device="cuda"), torch.tensor(C, device="cuda"))
+    warm = solver.solve_shared(*args, prec="fp32_refine")
+    cold = solver.solve_shared(*args, prec="fp64")          # the FP64 path starts every LP from the slack basis
+    torch.cuda.synchronize()
+    assert torch.equal(warm.status, cold.status)
+    rel = ((warm.obj - cold.obj).abs() / (1 + cold.obj.abs())).max().item()
+    assert rel <= 1e-8
+    ok = cold.status == 0
+    assert warm.iters[ok].float().mean().item() < 0.5 * cold.iters[ok].float().mean().item()
+    _check(A, b, C[:300], solver.solve_shared(args[0], args[1], args[2][:300].contiguous(), prec="fp32_refine"),
+           1e-8)
