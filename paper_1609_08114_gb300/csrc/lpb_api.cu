@@ -126,12 +126,25 @@ lpb_err make_pass(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   if (fit_rows > rows) fit_rows = rows;
   if (o->kernel == LPB_KERNEL_SMEM && fit_rows < rows) return LPB_EUNSUPPORTED;
   if (o->kernel == LPB_KERNEL_GMEM) fit_rows = 0;
+  // With many LPs, two CTAs per SM hide more latency than shared memory saves:
+  // when the whole tableau would leave room for fewer than two CTAs per SM,
+  // every row goes to the L2 slot and the CTAs take 512 threads (two per SM).
+  int auto_threads_override = 0;
+  if (o->kernel == LPB_KERNEL_AUTO && o->threads == 0 && b->count >= 16 * d.sms) {
+    const size_t all_smem = fixed + rows * rowb;
+    const int ctas = all_smem <= budget ? int(size_t(232448) / (all_smem + 1024)) : 0;
+    if (ctas < 2) {
+      fit_rows = 0;
+      auto_threads_override = 512;
+    }
+  }
   p->tab_smem = fit_rows * rowb;
   p->slot_bytes = ((rows - fit_rows) * rowb + 127) & ~size_t(127);
   p->gmem = p->slot_bytes > 0;
   p->smem = fixed + p->tab_smem;
   if (p->smem < 16) p->smem = 16;
-  p->threads = o->threads > 0 ? o->threads : auto_threads(eb, int(rows), int(rowb / eb), p->smem);
+  p->threads = o->threads > 0 ? o->threads
+             : auto_threads_override ? auto_threads_override : auto_threads(eb, int(rows), int(rowb / eb), p->smem);
   if (p->threads < 32 || p->threads > 1024 || (p->threads & 31)) return LPB_EINVAL;
   int occ = 0;
   if (tableau_max_ctas_per_sm(eb, p->threads, p->smem, &occ) != cudaSuccess) return LPB_ECUDA;
