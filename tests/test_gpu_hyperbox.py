@@ -65,3 +65,34 @@ def test_full_size_sampled(solver):
         idx = np.concatenate([np.arange(0, count, 997), np.arange(count - 40, count)])
         ref, _ = ohb.support(c[idx], l[idx], u[idx])
         assert np.array_equal(obj[idx], ref)
+
+
+def test_fp64_products_round_like_ieee(solver):
+    """The FP64 kernel forms each rounded product in integer arithmetic; crafted pairs hit
+    exact ties (round to even, both ways), carries into the exponent, the edges of the normal
+    range, subnormals, zeros and signed zeros.  The oracle's float64 loop is IEEE."""
+    eps = 2.0 ** -52
+    pairs = [(1 + eps, 1.5), (1 + 3 * eps, 1.5), (1 + eps, 1 + eps), (2 - eps, 1 + eps), (2 - eps, 2 - eps),
+             (1.5, 1 + 2 * eps), (3.0, 1 / 3), (2.0 ** 1000, 2.0 ** 23.5), (2.0 ** -1000, 2.0 ** -22),
+             (2.0 ** -1022, 0.75), (2.0 ** -1074, 3.0), (2.0 ** 1023, 1.999), (1e300, 1e10), (-0.0, 5.0),
+             (0.0, -7.0), (-(1 + eps), 1.5), (np.nextafter(1.0, 2.0), np.nextafter(1.0, 0.0)),
+             (1.0000000000000002, 0.9999999999999999), (2.0 ** -511, 2.0 ** -511), (2.0 ** -512, 2.0 ** -511)]
+    rng = np.random.default_rng(3)
+    n = 8
+    c = np.zeros((len(pairs) * 4, n))
+    l = np.full_like(c, -1.0)
+    u = np.full_like(c, 1.0)
+    for k, (a, b) in enumerate(pairs):
+        for s in range(4):                     # each pair in its own LP, with both signs of c
+            r = 4 * k + s
+            sa = -1.0 if s & 1 else 1.0
+            c[r, s] = sa * a
+            if sa < 0:
+                l[r, s] = -b
+            else:
+                u[r, s] = b
+            c[r, 4:] = rng.normal(size=4)
+    obj, x = _run(solver, c, l, u)
+    ref, h = ohb.support(c, l, u)
+    assert np.array_equal(obj.view(np.uint64), ref.view(np.uint64))
+    assert np.array_equal(x, h)
