@@ -418,14 +418,22 @@ def secondary_legs(solver, dev):
     A1 = 0.1 + 0.9 * torch.rand((100, 100), generator=g, device=dev, dtype=torch.float64)
     b1 = 1 + 9 * torch.rand(100, generator=g, device=dev, dtype=torch.float64)
     C1 = torch.rand((50_000, 100), generator=g, device=dev, dtype=torch.float64)
-    leg = {"count": 50_000, "m": 100, "n": 100}
-    for prec in ("fp32_refine", "fp64"):
-        r = solver.solve_shared(A1, b1, C1, prec=prec)
-        ms = _time(lambda: solver.solve_shared(A1, b1, C1, prec=prec, out=r), reps=3)
-        leg[prec] = {"LPs_per_s": 50_000 / (ms * 1e-3), "ms": ms, "pivots_per_lp": float(r.iters.float().mean()),
-                     "statuses": {str(k): int(v) for k, v in zip(*np.unique(r.status.cpu().numpy(), return_counts=True))}}
-    out["shared_polytope_50000x100"] = leg
-    del A1, b1, C1
+    # and directions that turn smoothly (a sweep, as when a support function is sampled
+    # along an ordered set of template directions): c_k = c_0 + 1e-4 k d
+    c0 = torch.rand(100, generator=g, device=dev, dtype=torch.float64)
+    dd = torch.randn(100, generator=g, device=dev, dtype=torch.float64)
+    C2 = c0[None, :] + 1e-4 * torch.arange(50_000, device=dev, dtype=torch.float64)[:, None] * dd[None, :]
+    for name, C in (("shared_polytope_50000x100_random_dirs", C1), ("shared_polytope_50000x100_sweep_dirs", C2)):
+        leg = {"count": 50_000, "m": 100, "n": 100}
+        for prec in ("fp32_refine", "fp64"):
+            r = solver.solve_shared(A1, b1, C, prec=prec)
+            ms = _time(lambda: solver.solve_shared(A1, b1, C, prec=prec, out=r), reps=3)
+            leg[prec] = {"LPs_per_s": 50_000 / (ms * 1e-3), "ms": ms, "pivots_per_lp": float(r.iters.float().mean()),
+                         "resolved_fp64": solver.stats()["resolved_fp64"],
+                         "statuses": {str(k): int(v) for k, v in zip(*np.unique(r.status.cpu().numpy(),
+                                                                                return_counts=True))}}
+        out[name] = leg
+    del A1, b1, C1, C2
     torch.cuda.empty_cache()
     # 10,000 x m=n=200 two-phase
     sb = synth.type2(10_000, 200, 200, seed=2)
