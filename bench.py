@@ -8,7 +8,8 @@ refinement and KKT certificate, FP64 re-solve of failures, outputs.  Prints one 
 Secondary legs (skip with ``--no-legs``) time the other workloads once each with CUDA
 events: 1,000 x m=n=16; the m=n sweep; the two Step 1 rules (most negative reduced cost
 vs a random eligible column) on 50,000 x m=n=100; one m=n=100 polytope in 50,000
-directions (shared constraints); 10,000 x m=n=200 two-phase; hyperbox
+directions (shared constraints); 10,000 x m=n=100 with bounds l <= x <= u; 10,000 x m=n=200
+two-phase; hyperbox
 support functions (4,000,000 x 5 FP32, 6,000,000 x 28 FP64); 20,000 mixed sizes forward
 and forward+backward.
 
@@ -434,6 +435,21 @@ def secondary_legs(solver, dev):
                                                                                 return_counts=True))}}
         out[name] = leg
     del A1, b1, C1, C2
+    torch.cuda.empty_cache()
+    # bounded variables: 10,000 x m=n=100, l ~ U[-1,0], u = l + U[0.5,2] (m + n rows once reduced)
+    bt = _type1_device(10_000, 100, 100, dev, seed=7)
+    g = torch.Generator(device=dev)
+    g.manual_seed(8)
+    lo = -torch.rand(bt.c.numel(), generator=g, device=dev, dtype=torch.float64)
+    hi = lo + 0.5 + 1.5 * torch.rand(bt.c.numel(), generator=g, device=dev, dtype=torch.float64)
+    leg = {"count": 10_000, "m": 100, "n": 100}
+    for prec in ("fp32_refine", "fp64"):
+        r = solver.solve_bounded(bt, lo, hi, prec=prec)
+        ms = _time(lambda: solver.solve_bounded(bt, lo, hi, prec=prec, out=r), reps=3)
+        leg[prec] = {"LPs_per_s": 10_000 / (ms * 1e-3), "ms": ms, "pivots_per_lp": float(r.iters.float().mean()),
+                     "statuses": {str(k): int(v) for k, v in zip(*np.unique(r.status.cpu().numpy(), return_counts=True))}}
+    out["bounded_10000x100"] = leg
+    del bt, lo, hi
     torch.cuda.empty_cache()
     # 10,000 x m=n=200 two-phase
     sb = synth.type2(10_000, 200, 200, seed=2)

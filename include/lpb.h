@@ -244,6 +244,28 @@ lpb_err lpb_solve_shared(lpb_handle *handle, int32_t m, int32_t n, int32_t dtype
                          int64_t count, const void *C, const lpb_options *opt, const lpb_result *result,
                          void *ws, size_t ws_bytes, void *stream);
 
+/* Bounded variables: for every LP of the batch
+ *
+ *     maximize  c^T x   subject to  A x <= b,  l <= x <= u,
+ *
+ * with l and u (device, FP64, packed like c) in place of x >= 0; l must be
+ * finite, u may be +inf.  Solved exactly through the change of variables
+ * x = l + z: max c^T z + c^T l subject to A z <= b - A l (formed in FP64),
+ * z_j <= u_j - l_j (the row 0 <= 1 when u_j = +inf) and z >= 0 -- an LP of
+ * m + n rows that lpb_solve's passes handle (all precisions and pivot rules;
+ * an empty box or b - A l < 0 goes through Phase I).  The batch must be FP64
+ * (LPB_EUNSUPPORTED otherwise).  Results: status, iters, obj and x of the
+ * bounded LP (x = l + z), y the duals of A x <= b (nullable); result->basis
+ * must be NULL (LPB_EINVAL), the basis of the reduced LP having m + n rows.
+ * `ws` is device memory of lpb_workspace_size_bounded() bytes (the reduced
+ * batch at a fixed stride of (max_m + max_n) x max_n per LP, plus a solve
+ * workspace), 256-byte aligned.  Asynchronous on `stream`. */
+lpb_err lpb_workspace_size_bounded(lpb_handle *handle, const lpb_batch *batch, const lpb_options *opt,
+                                   size_t *bytes);
+lpb_err lpb_solve_bounded(lpb_handle *handle, const lpb_batch *batch, const void *l, const void *u,
+                          const lpb_options *opt, const lpb_result *result, void *ws, size_t ws_bytes,
+                          void *stream);
+
 /* lpb_solve for callers that cannot allocate device memory.  The paper has no
  * counterpart; this exists for plug-ins whose host framework owns all device
  * memory through its own pool, and for loops where cudaMalloc / cudaFree are

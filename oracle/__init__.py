@@ -7,6 +7,8 @@ benchmark's CPU-baseline leg may import this package.
 
 * :func:`solve_batch` / :func:`solve_one` -- the two-phase dense-tableau simplex
   of Section 3 (``simplex_oracle.c``, compiled with gcc, OpenMP over LPs).
+* :func:`solve_bounded_batch` -- ``l <= x <= u`` in place of ``x >= 0``, by the change of
+  variables ``x = l + z`` and one row ``z_j <= u_j - l_j`` per finite upper bound.
 * :mod:`oracle.brute` -- vertex / extreme-ray enumeration for tiny LPs.
 * :mod:`oracle.hyperbox` -- the closed form of Section 6, Eq. 8, in a fixed
   summation order.
@@ -150,3 +152,40 @@ def solve_batch(batch, max_iter: int = 0, eps_p: float = EPS_P, eps_d: float = E
                                         _p(status), _p(x), _p(y), _p(obj), _p(basis), _p(iters), int(rule),
                                         int(seed), int(first_lp))
     return dict(status=status, x=x, y=y, obj=obj, basis=basis[:b.size], iters=iters)
+
+
+def solve_bounded_batch(batch, l, u, nthreads: int = 0, **kw):
+    """Every LP ``max c^T x, A x <= b, l <= x <= u`` of a packed batch, ``l`` and ``u``
+    packed like ``c`` (``l`` finite, ``u`` may be ``+inf``).  With ``x = l + z`` the LP
+    is ``max c^T z + c^T l`` subject to ``A z <= b - A l``, ``z_j <= u_j - l_j`` for every
+    finite ``u_j`` and ``z >= 0``, which :func:`solve_batch` solves; the results map back
+    to ``x = l + z``, ``obj + c^T l`` and the duals of the rows of ``A``."""
+    import synth
+    l = np.asarray(l, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    lps, fin = [], []
+    for k in range(len(batch.m)):
+        A, b, c = batch.lp(k)
+        m, n = A.shape
+        lk = l[batch.c_off[k]:batch.c_off[k] + n]
+        uk = u[batch.c_off[k]:batch.c_off[k] + n]
+        f = np.isfinite(uk)
+        A2 = np.vstack([A, np.eye(n)[f]])
+        b2 = np.concatenate([b - A @ lk, (uk - lk)[f]])
+        lps.append((A2, b2, c))
+        fin.append((m, n, lk, c))
+    r = solve_batch(synth.pack(lps), nthreads=nthreads, **kw)
+    cnt = len(batch.m)
+    out = dict(status=r["status"].copy(), obj=r["obj"].copy(), iters=r["iters"].copy(),
+               x=np.zeros(np.asarray(batch.c).size), y=np.zeros(np.asarray(batch.b).size))
+    xo = yo = 0
+    for k in range(cnt):
+        m, n, lk, c = fin[k]
+        m2 = lps[k][0].shape[0]
+        if out["status"][k] == OPTIMAL:
+            out["x"][batch.c_off[k]:batch.c_off[k] + n] = r["x"][xo:xo + n] + lk
+            out["y"][batch.b_off[k]:batch.b_off[k] + m] = r["y"][yo:yo + m]
+            out["obj"][k] += float(c @ lk)
+        xo += n
+        yo += m2
+    return out

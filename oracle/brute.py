@@ -67,3 +67,29 @@ def solve(A, b, c, tol: float = 1e-9):
     vals = [float(c @ v) for v in V]
     k = int(np.argmax(vals))
     return OPTIMAL, vals[k], V[k]
+
+
+def solve_box(A, b, c, l, u, tol: float = 1e-9):
+    """Return ``(status, obj, x)`` for ``max c^T x, A x <= b, l <= x <= u`` with finite
+    bounds by enumeration: the region is a polytope, so it is empty (infeasible) or
+    ``c^T x`` attains its maximum at a vertex, where ``n`` linearly independent
+    constraints of ``G x <= h`` (the rows of A, x <= u and -x <= -l) are tight."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    G = np.vstack([A, np.eye(n), -np.eye(n)])
+    h = np.concatenate([np.asarray(b, dtype=np.float64), np.asarray(u, dtype=np.float64),
+                        -np.asarray(l, dtype=np.float64)])
+    c = np.asarray(c, dtype=np.float64)
+    best, bx = -np.inf, None
+    for S in itertools.combinations(range(G.shape[0]), n):
+        Gs = G[list(S)]
+        if abs(np.linalg.det(Gs)) < 1e-12:
+            continue
+        x = np.linalg.solve(Gs, h[list(S)])
+        if np.all(G @ x <= h + tol * (1 + np.abs(h))):
+            v = float(c @ x)
+            if v > best:
+                best, bx = v, x
+    if bx is None:
+        return INFEASIBLE, -np.inf, None
+    return OPTIMAL, best, bx

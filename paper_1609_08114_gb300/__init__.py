@@ -226,6 +226,29 @@ class Solver:
                    "lpb_solve_shared")
         return res
 
+    def solve_bounded(self, batch: LPBatch, l: torch.Tensor, u: torch.Tensor, prec="fp32_refine",
+                      out: SolveResult | None = None, **kw) -> SolveResult:
+        """Every LP ``max c^T x, A x <= b, l <= x <= u`` of an FP64 ``batch`` (lpb_solve_bounded);
+        ``l`` (finite) and ``u`` (``+inf`` allowed) are packed like ``c``.  The result has no basis."""
+        if l.dtype != torch.float64 or u.dtype != torch.float64 or batch.A.dtype != torch.float64:
+            raise ValueError("solve_bounded takes an FP64 batch and FP64 bounds")
+        opt = self.options(prec, **kw)
+        dev = batch.device
+        res = out if out is not None else SolveResult(
+            torch.empty(batch.count, dtype=torch.int32, device=dev), torch.empty(batch.count, dtype=torch.int32, device=dev),
+            torch.empty(batch.count, dtype=torch.float64, device=dev),
+            torch.empty(batch.c.numel(), dtype=torch.float64, device=dev),
+            torch.empty(batch.b.numel(), dtype=torch.float64, device=dev), None)
+        cb, cr = batch.cstruct(), res.cstruct()
+        nb = ctypes.c_size_t()
+        _lib.check(self.lib.lpb_workspace_size_bounded(self.h, ctypes.byref(cb), ctypes.byref(opt), ctypes.byref(nb)),
+                   "lpb_workspace_size_bounded")
+        ws = self.workspace(int(nb.value))
+        _lib.check(self.lib.lpb_solve_bounded(self.h, ctypes.byref(cb), _ptr(l.contiguous()), _ptr(u.contiguous()),
+                                              ctypes.byref(opt), ctypes.byref(cr), _ptr(ws), ws.numel(),
+                                              _stream_handle(self.device)), "lpb_solve_bounded")
+        return res
+
     def autotune(self, batch: LPBatch, prec="fp32_refine", table_path: str | None = None,
                  out: SolveResult | None = None, **kw) -> float:
         """Pick the fastest schedule for batches shaped like ``batch`` (lpb_autotune); later solves

@@ -69,6 +69,10 @@ SIGNATURES = {
                                                  ctypes.POINTER(Options), ctypes.POINTER(ctypes.c_size_t)]),
     "lpb_solve_shared": (ctypes.c_int, [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, ctypes.c_int64, P,
                                         ctypes.POINTER(Options), ctypes.POINTER(Result), P, ctypes.c_size_t, P]),
+    "lpb_workspace_size_bounded": (ctypes.c_int, [P, ctypes.POINTER(Batch), ctypes.POINTER(Options),
+                                                  ctypes.POINTER(ctypes.c_size_t)]),
+    "lpb_solve_bounded": (ctypes.c_int, [P, ctypes.POINTER(Batch), P, P, ctypes.POINTER(Options),
+                                         ctypes.POINTER(Result), P, ctypes.c_size_t, P]),
     "lpb_hyperbox": (ctypes.c_int, [P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P, P, P,
                                     ctypes.c_int32, P, P, P]),
     "lpb_autotune": (ctypes.c_int, [P, ctypes.POINTER(Batch), ctypes.POINTER(Options), ctypes.POINTER(Result), P,

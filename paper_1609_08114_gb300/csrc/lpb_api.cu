@@ -563,6 +563,104 @@ lpb_err make_shared_plan(const DeviceInfo &d, int m, int n, int dtype, int64_t c
 
 }  // namespace
 
+// ---- bounded variables: l <= x <= u in place of x >= 0 ----------------------
+
+namespace {
+
+// Change of variables x = l + z: LP k becomes max c^T z subject to
+// A z <= b - A l and z_j <= u_j - l_j (the row 0 <= 1 when u_j = +inf), z >= 0,
+// written in FP64 at a fixed stride per LP.  One CTA per LP (grid-stride).
+template <typename T>
+__global__ void bounded_transform(BatchDev B, const T *l, const T *u, int mm, int nn, double *A2, double *b2,
+                                  int32_t *m2, int32_t *n2, int64_t *a2_off, int64_t *b2_off, int64_t *c2_off) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const T *A = static_cast<const T *>(B.A), *b = static_cast<const T *>(B.b);
+  for (int k = blockIdx.x; k < B.count; k += gridDim.x) {
+    const int m = B.m[k], n = B.n[k];
+    const int64_t ao = B.a_off[k], bo = B.b_off[k], co = B.c_off[k];
+    const int64_t sa = int64_t(k) * (mm + nn) * nn, sb = int64_t(k) * (mm + nn);
+    const bool ok = m >= 1 && n >= 1 && m <= mm && n <= nn;
+    if (threadIdx.x == 0) {
+      m2[k] = ok ? m + n : 0;         // a size of 0 reports LPB_BAD_SIZE
+      n2[k] = ok ? n : 0;
+      a2_off[k] = sa;
+      b2_off[k] = sb;
+      c2_off[k] = co;
+    }
+    if (!ok) continue;
+    for (int64_t t = threadIdx.x; t < int64_t(m) * n; t += blockDim.x) A2[sa + t] = double(A[ao + t]);
+    for (int64_t t = threadIdx.x; t < int64_t(n) * n; t += blockDim.x) {   // row z_j <= u_j - l_j, or 0 <= 1
+      const int j = int(t / n);
+      const double uj = double(u[co + j]);
+      A2[sa + int64_t(m) * n + t] = (j == int(t % n) && !(isinf(uj) && uj > 0.0)) ? 1.0 : 0.0;
+    }
+    for (int i = wid; i < m; i += nw) {          // b_i - A_i l in FP64, one warp per row
+      double s = 0.0;
+      for (int j = lane; j < n; j += 32) s = fma(double(A[ao + int64_t(i) * n + j]), double(l[co + j]), s);
+      s = warp_sum(s);
+      if (lane == 0) b2[sb + i] = double(b[bo + i]) - s;
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double uj = double(u[co + j]), lj = double(l[co + j]);
+      b2[sb + m + j] = (isinf(uj) && uj > 0.0) ? 1.0 : uj - lj;
+    }
+  }
+}
+
+// Back to the bounded LP: x = l + z and obj + c^T l for optimal LPs; the duals
+// of the rows of A are the first m duals of the reduced LP.
+template <typename T>
+__global__ void bounded_finish(BatchDev B, const T *l, lpb_result R, const double *y2, int mm, int nn) {
+  const int lane = threadIdx.x & 31;
+  const T *c = static_cast<const T *>(B.c);
+  for (int k = blockIdx.x; k < B.count; k += gridDim.x) {
+    const int m = B.m[k], n = B.n[k];
+    if (m < 1 || n < 1 || m > mm || n > nn) continue;
+    const int64_t bo = B.b_off[k], co = B.c_off[k], sb = int64_t(k) * (mm + nn);
+    const bool opt = R.status[k] == LPB_OPTIMAL;
+    if (threadIdx.x < 32) {
+      double s = 0.0;
+      for (int j = lane; j < n; j += 32) s = fma(double(c[co + j]), double(l[co + j]), s);
+      s = warp_sum(s);
+      if (lane == 0 && opt) R.obj[k] += s;
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) R.x[co + j] = opt ? R.x[co + j] + double(l[co + j]) : 0.0;
+    if (R.y)
+      for (int i = threadIdx.x; i < m; i += blockDim.x) R.y[bo + i] = opt ? y2[sb + i] : 0.0;
+  }
+}
+
+struct BoundedPlan {
+  size_t o_A = 0, o_b = 0, o_y = 0, o_m = 0, o_n = 0, o_ao = 0, o_bo = 0, o_co = 0, o_ws = 0, solve_ws = 0, total = 0;
+};
+
+lpb_err make_bounded_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o, BoundedPlan *bp) {
+  if (!b || !o || b->count < 0 || b->max_m < 1 || b->max_n < 1) return LPB_EINVAL;
+  if (b->dtype != LPB_DTYPE_F64) return LPB_EUNSUPPORTED;   // the reduced LP reads the caller's c as FP64
+  if (b->max_m + b->max_n > kMaxDim) return LPB_EUNSUPPORTED;
+  lpb_batch rb = *b;
+  rb.max_m = b->max_m + b->max_n;
+  rb.dtype = LPB_DTYPE_F64;
+  const lpb_err e = solve_workspace_bytes(d, &rb, o, false, &bp->solve_ws);
+  if (e != LPB_OK) return e;
+  const size_t c = size_t(b->count > 0 ? b->count : 1), rows = size_t(b->max_m + b->max_n);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t at = off; off = align256(off + bytes); return at; };
+  bp->o_A = take(c * rows * size_t(b->max_n) * 8);
+  bp->o_b = take(c * rows * 8);
+  bp->o_y = take(c * rows * 8);
+  bp->o_m = take(c * 4);
+  bp->o_n = take(c * 4);
+  bp->o_ao = take(c * 8);
+  bp->o_bo = take(c * 8);
+  bp->o_co = take(c * 8);
+  bp->o_ws = take(bp->solve_ws);
+  bp->total = off;
+  return LPB_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *lpb_version(void) { return "liblpb 0.1 (sm_103a)"; }
@@ -853,6 +951,71 @@ lpb_err lpb_solve_shared(lpb_handle *h, int32_t m, int32_t n, int32_t dtype, con
   bt.c = C;
   return run_solve(d, h->d_ctr, h->d_err, &bt, o, r, w + sp.o_ws, sp.solve_ws, s, nullptr, nullptr,
                    &h->last_kernels, 0, dyo, 1);
+}
+
+lpb_err lpb_workspace_size_bounded(lpb_handle *h, const lpb_batch *b, const lpb_options *o, size_t *bytes) {
+  if (!h || !b || !o || !bytes) return LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  BoundedPlan bp;
+  const lpb_err e = make_bounded_plan(device_info(h), b, o, &bp);
+  if (e != LPB_OK) return e;
+  *bytes = bp.total;
+  return LPB_OK;
+}
+
+lpb_err lpb_solve_bounded(lpb_handle *h, const lpb_batch *b, const void *l, const void *u, const lpb_options *o,
+                          const lpb_result *r, void *ws, size_t ws_bytes, void *stream) {
+  if (!h || !b || !o || !r) return LPB_EINVAL;
+  if (b->count < 0) return LPB_EINVAL;
+  if (b->count == 0) return LPB_OK;
+  if (!b->m || !b->n || !b->a_off || !b->b_off || !b->c_off || !b->A || !b->b || !b->c || !l || !u)
+    return LPB_EINVAL;
+  if (!r->status || !r->obj || !r->x || r->basis) return LPB_EINVAL;   // the basis has m + n rows here
+  if (b->dtype != LPB_DTYPE_F64) return b->dtype == LPB_DTYPE_F32 ? LPB_EUNSUPPORTED : LPB_EINVAL;
+  DeviceScope ds(h->device);
+  if (!ds.ok()) return LPB_ECUDA;
+  const DeviceInfo d = device_info(h);
+  BoundedPlan bp;
+  lpb_err e = make_bounded_plan(d, b, o, &bp);
+  if (e != LPB_OK) return e;
+  if (ws_bytes < bp.total || !ws) return LPB_ENOMEM;
+  if (reinterpret_cast<uintptr_t>(ws) & 255) return LPB_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned char *w = static_cast<unsigned char *>(ws);
+  double *A2 = reinterpret_cast<double *>(w + bp.o_A), *b2 = reinterpret_cast<double *>(w + bp.o_b);
+  double *y2 = reinterpret_cast<double *>(w + bp.o_y);
+  int32_t *m2 = reinterpret_cast<int32_t *>(w + bp.o_m), *n2 = reinterpret_cast<int32_t *>(w + bp.o_n);
+  int64_t *ao = reinterpret_cast<int64_t *>(w + bp.o_ao), *bo = reinterpret_cast<int64_t *>(w + bp.o_bo);
+  int64_t *co = reinterpret_cast<int64_t *>(w + bp.o_co);
+  const BatchDev bd{b->count, b->max_m, b->max_n, b->dtype, b->m, b->n, b->a_off, b->b_off, b->c_off, b->A, b->b, b->c};
+  const int grid = b->count < 8 * d.sms ? b->count : 8 * d.sms;
+  bounded_transform<double><<<grid, 256, 0, s>>>(bd, static_cast<const double *>(l), static_cast<const double *>(u),
+                                                 b->max_m, b->max_n, A2, b2, m2, n2, ao, bo, co);
+  if (cudaGetLastError() != cudaSuccess) return LPB_ECUDA;
+  // The reduced batch: FP64 data (A is exact, b - A l is formed in FP64), the
+  // caller's objectives (c offsets unchanged), results into the caller's x.
+  lpb_batch rb{};
+  rb.count = b->count;
+  rb.max_m = b->max_m + b->max_n;
+  rb.max_n = b->max_n;
+  rb.dtype = LPB_DTYPE_F64;
+  rb.m = m2;
+  rb.n = n2;
+  rb.a_off = ao;
+  rb.b_off = bo;
+  rb.c_off = co;
+  rb.A = A2;
+  rb.b = b2;
+  rb.c = b->c;
+  lpb_result rr = *r;
+  rr.y = y2;
+  rr.basis = nullptr;
+  e = run_solve(d, h->d_ctr, h->d_err, &rb, o, &rr, w + bp.o_ws, bp.solve_ws, s, nullptr, nullptr,
+                &h->last_kernels);
+  if (e != LPB_OK) return e;
+  bounded_finish<double><<<grid, 256, 0, s>>>(bd, static_cast<const double *>(l), *r, y2, b->max_m, b->max_n);
+  return cudaGetLastError() == cudaSuccess ? LPB_OK : LPB_ECUDA;
 }
 
 lpb_err lpb_autotune(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const lpb_result *r,
