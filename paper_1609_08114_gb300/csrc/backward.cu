@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BackwardParams P)
   int *slist = reinterpret_cast<int *>(smem + L.slist);
   int *nlist = reinterpret_cast<int *>(smem + L.nlist);
   double *vN = reinterpret_cast<double *>(smem + L.v);
-  __shared__ int s_item, s_k, s_kn, s_ok, s_piv;
+  __shared__ int s_item, s_k, s_kn, s_ok;
   __shared__ double s_redv[32];
   __shared__ int s_redk[32];
   const int dt = P.B.dtype;
