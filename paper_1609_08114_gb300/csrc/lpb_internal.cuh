@@ -146,6 +146,18 @@ __device__ __forceinline__ void warp_argmin_f32(float &v, int &k) {
 template <>
 __device__ __forceinline__ void warp_argmin<float>(float &v, int &k) { warp_argmin_f32(v, k); }
 
+// Maximum of a 64-bit unsigned value over the warp (every lane takes part)
+// with two warp-reduction instructions: the largest high word, then the
+// largest low word among the lanes holding it.  Non-negative doubles order
+// like their bit patterns, so this is also the maximum of such doubles.  A
+// warp then makes one shared-memory atomic instead of one per thread (same-
+// address 64-bit atomics serialise).
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+  const unsigned hi = __reduce_max_sync(kFull, unsigned(v >> 32));
+  const unsigned lo = __reduce_max_sync(kFull, unsigned(v >> 32) == hi ? unsigned(v) : 0u);
+  return (static_cast<unsigned long long>(hi) << 32) | lo;
+}
+
 // Every thread of the block receives the block-wide minimum.  `bv`/`bk` hold
 // one slot per warp; a call site must not reuse them before the block has
 // passed another __syncthreads().

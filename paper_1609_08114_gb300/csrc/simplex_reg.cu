@@ -88,15 +88,14 @@ __device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(lo), "r"(unsigned(hi - lo)) : "memory");
 }
 
-// Prefetch A, b and c of work item `item` into L2 when the LP fits the launch.
-__device__ __forceinline__ void prefetch_lp(const TableauParams &P, int item) {
-  const int lp = P.in.items ? P.in.items[item] : item;
-  const int m = P.B.m[lp], n = P.B.n[lp];
+// Prefetch A, b and c of an LP into L2 when it fits the launch.
+__device__ __forceinline__ void prefetch_lp(const TableauParams &P, int m, int n, long long aoff, long long boff,
+                                            long long coff) {
   if (m < 1 || n < 1 || m > P.lim_m || n > P.lim_n || m > P.B.max_m || n > P.B.max_n) return;
   const size_t es = P.B.dtype == LPB_DTYPE_F64 ? 8 : 4;
-  prefetch_l2(static_cast<const unsigned char *>(P.B.A) + size_t(P.B.a_off[lp]) * es, size_t(m) * size_t(n) * es);
-  prefetch_l2(static_cast<const unsigned char *>(P.B.b) + size_t(P.B.b_off[lp]) * es, size_t(m) * es);
-  prefetch_l2(static_cast<const unsigned char *>(P.B.c) + size_t(P.B.c_off[lp]) * es, size_t(n) * es);
+  prefetch_l2(static_cast<const unsigned char *>(P.B.A) + size_t(aoff) * es, size_t(m) * size_t(n) * es);
+  prefetch_l2(static_cast<const unsigned char *>(P.B.b) + size_t(boff) * es, size_t(m) * es);
+  prefetch_l2(static_cast<const unsigned char *>(P.B.c) + size_t(coff) * es, size_t(n) * es);
 }
 
 // Step 1-2 result of one warp for one pivot: its best entering column and
@@ -113,6 +112,13 @@ __device__ __forceinline__ double vin(const double *v, int i, int dt) {
   return dt == LPB_DTYPE_F64 ? v[i] : double(reinterpret_cast<const float *>(v)[i]);
 }
 
+// A claimed work item and its LP's sizes and offsets, as the claimer thread
+// gathers them by asynchronous copies while the LP before it is solved.
+struct RegDesc {
+  long long aoff, boff, coff;
+  int item, lp, m, n;
+};
+
 template <int R, int C, int W>
 struct RegShared {
   static constexpr int ROWS = 32 * R, COLS = W * C;
@@ -124,9 +130,11 @@ struct RegShared {
   int basic[ROWS];
   int nonb[COLS];
   alignas(16) float objv[W][(C + 3) & ~3];   // objective row, per warp
-  int item, nsb, nns;
+  RegDesc desc[2];                           // this LP's and the next one's, by LP parity
+  int cstage;                                // how far the next LP's descriptor has come
+  int nsb, nns;
   int warm_ok;                               // shared constraints: start from the previous basis
-  unsigned long long bmax, cmax;
+  unsigned long long wbmax[W], wcmax[W];     // |b|max and |c|max bits, per warp
   uint64_t abar;                             // completion of the bulk copies of A
   double xb[ROWS], rr[ROWS], yv[ROWS], sax[ROWS], dj[COLS];
   float part[W][ROWS];
@@ -135,6 +143,7 @@ struct RegShared {
   int sb[ROWS], jb[ROWS], sp[ROWS];
   int ns[COLS], kr[COLS];
   double red[2][W];
+  double tpd[2];                             // the certificate's primal and dual tolerances
 };
 
 template <int R, int C, int W>
@@ -263,8 +272,13 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     fence_mbar_init();
   }
   unsigned aphase = 0;        // parity of the next completion of sh.abar
-  // Lane 0 of the last warp claims work items one LP ahead, so that the next
-  // LP's data can be prefetched into L2 while this one is solved.
+  // Lane 0 of the last warp claims work items one LP ahead.  Each global round
+  // trip of the claim waits a phase of the current LP before it is used: the
+  // queue atomic when an LP starts; the item's LP index (stage 1) after the
+  // tableau is built; its sizes and offsets (stage 2) after the pivots; an L2
+  // prefetch of its data (stage 3) during the refinement.  Stages 1 and 2 copy
+  // into the descriptor slot of the next LP asynchronously; an LP that ends
+  // early has its remaining stages done when the next one starts.
   const int claimer = NT - 32;
   // A shared-constraint batch (one A and b, many objectives) is claimed in
   // chunks of consecutive objectives, so that a CTA starts each objective from
@@ -277,7 +291,44 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     return atomicAdd(P.queue, 1);
   };
   int next = 0;
-  if (tid == claimer) next = claim(-1);
+  int slot = 0;                 // descriptor slot of the current LP (same in every thread)
+  auto stage1 = [&]() {         // claimer: item and LP index of the claimed item
+    RegDesc &d = sh.desc[slot ^ 1];
+    d.item = next;
+    if (next < nitems) {
+      if (P.in.items) cp_async4(&d.lp, P.in.items + next);
+      else d.lp = next;
+    }
+    sh.cstage = 1;
+  };
+  auto stage2 = [&]() {         // claimer: sizes and offsets
+    cp_async_wait_all();
+    RegDesc &d = sh.desc[slot ^ 1];
+    if (d.item < nitems) {
+      const int l = d.lp;
+      cp_async4(&d.m, P.B.m + l);
+      cp_async4(&d.n, P.B.n + l);
+      cp_async8(&d.aoff, P.B.a_off + l);
+      cp_async8(&d.boff, P.B.b_off + l);
+      cp_async8(&d.coff, P.B.c_off + l);
+    }
+    sh.cstage = 2;
+  };
+  auto stage3 = [&]() {         // claimer: L2 prefetch of the next LP's data
+    cp_async_wait_all();
+    const RegDesc &d = sh.desc[slot ^ 1];
+    if (d.item < nitems && !P.shared) prefetch_lp(P, d.m, d.n, d.aoff, d.boff, d.coff);
+    sh.cstage = 3;
+  };
+  if (tid == claimer) {
+    next = claim(-1);
+    slot = 1;                   // the first LP's descriptor goes to slot 0
+    stage1();
+    stage2();
+    cp_async_wait_all();
+    slot = 0;
+  }
+  slot = 0;
   // The basis of the last tableau: every lane keeps, for its rows lane + 32 r,
   // the basic variable and the right-hand side (the same FP32 values warp W-1
   // holds in its last column); lane c < C keeps the variable of the warp's
@@ -288,18 +339,26 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
   int nvar = kBad >> kIdxBits;
   int valid_tab = 0, warm_run = 0;
   int sld_res = sld_pad;                       // row stride of the resident A
-  for (;;) {
-    if (tid == claimer) sh.item = next;
+  for (int first = 1;; first = 0) {
+    if (tid == claimer && !first) {   // stages the last LP did not reach; its slot becomes current
+      const int st = sh.cstage;
+      if (st < 1) stage1();
+      if (st < 2) stage2();
+      if (st < 3) stage3();
+      cp_async_wait_all();
+    }
+    if (!first) slot ^= 1;
     if (tid == 0) sh.warm_ok = P.shared && valid_tab && warm_run < kWarmMax;
     __syncthreads();
-    const int item = sh.item;
+    const RegDesc &D = sh.desc[slot];
+    const int item = D.item;
     if (item >= nitems) break;
     const bool warm = sh.warm_ok != 0;     // keep the basis; load and price only the new objective
     warm_run = warm ? warm_run + 1 : 0;
     valid_tab = 0;
-    const int lp = P.in.items ? P.in.items[item] : item;
-    const int m = P.B.m[lp], n = P.B.n[lp];
-    const int64_t aoff = P.B.a_off[lp], boff = P.B.b_off[lp], coff = P.B.c_off[lp];
+    const int lp = D.lp;
+    const int m = D.m, n = D.n;
+    const int64_t aoff = D.aoff, boff = D.boff, coff = D.coff;
     // ---- admission: sizes that fit the template, b >= 0, finite b and c ----
     const bool fits = m >= 1 && n >= 1 && m <= ROWS - 1 && n <= COLS - 1 && m <= P.B.max_m && n <= P.B.max_n &&
                       m <= P.lim_m && n <= P.lim_n;
@@ -371,13 +430,9 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     }
     if (tid == claimer) {
       next = claim(item);
-      if (next < nitems && !P.shared) prefetch_lp(P, next);
+      sh.cstage = 0;
     }
     int neg = 0;
-    if (tid == 0) {
-      if (!warm) sh.bmax = 0ull;          // a warm start keeps b and its |b|max
-      sh.cmax = 0ull;
-    }
     cp_async_wait_all();
     int timed_out = 0;
     if (dense || bulk || bulk_bc || bulk_c) {
@@ -420,8 +475,12 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
         neg |= int(a >= kInf);
         cm = a > cm ? a : cm;
       }
-      if (bm > 0ull && bm <= kInf) atomicMax(&sh.bmax, bm);
-      if (cm > 0ull && cm < kInf) atomicMax(&sh.cmax, cm);
+      bm = warp_max_u64(bm <= kInf ? bm : 0ull);      // NaN magnitudes take no part
+      cm = warp_max_u64(cm < kInf ? cm : 0ull);
+      if (lane == 0) {                               // a warm start keeps b and its |b|max
+        if (!warm) sh.wbmax[wid] = bm;
+        sh.wcmax[wid] = cm;
+      }
     }
     neg = __syncthreads_or(neg);
     if (!fits || neg) {      // the shared-memory kernel handles it (Phase I, sizes, bad data)
@@ -432,8 +491,6 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       __syncthreads();
       continue;
     }
-    const double bmax = __longlong_as_double(static_cast<long long>(sh.bmax));
-    const double cmax = __longlong_as_double(static_cast<long long>(sh.cmax));
 
     // ---- the tableau: A rounded to FP32, b in column COLS-1, -c in row ROWS-1 ----
     int bad = 0;
@@ -529,6 +586,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
 
     valid_tab = 1;
 
+    if (tid == claimer) stage1();
     // ---- Steps 1-3, one block barrier per pivot ----
     // Each warp takes its own best entering column (Step 1 over its columns)
     // and runs the min-ratio test on it (Step 2); after the barrier every warp
@@ -664,6 +722,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       }
     }
     if (lane < C) sh.nonb[wid + W * lane] = nvar;
+    if (tid == claimer) stage2();
     __syncthreads();
 
     const int64_t yoff = P.R.y_off ? P.R.y_off[lp] : boff;    // outputs packed like b, or at y_off
@@ -751,6 +810,15 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       sh.xb[i] = i < m ? double(sh.rhs[i]) : 0.0;
     }
     for (int j = tid; j < COLS; j += NT) sh.posx[j] = -1;
+    if (tid == 0) {        // FP64 work is scarce here: one thread, not every warp
+      unsigned long long bm = 0ull, cm = 0ull;
+      for (int w = 0; w < W; ++w) {
+        bm = max(bm, sh.wbmax[w]);
+        cm = max(cm, sh.wcmax[w]);
+      }
+      sh.tpd[0] = P.feas_tol * (1.0 + __longlong_as_double(static_cast<long long>(bm)));
+      sh.tpd[1] = P.feas_tol * (1.0 + __longlong_as_double(static_cast<long long>(cm)));
+    }
     __syncthreads();
     const int nsb = sh.nsb, nns = sh.nns;
     for (int i = tid; i < m; i += NT) {
@@ -758,14 +826,14 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       if (v >= n) sh.sp[v - n] = i;
       else sh.posx[v] = i;
     }
-    if (lane == 31) {
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        if (wid == W - 1 && c == C - 1) continue;      // the right-hand side
-        const int v = sh.nonb[wid + W * c];
-        if (v >= n && v < n + m) sh.yv[v - n] = double(T[R - 1][c]);
+    // y of the non-basic slacks from the objective row that the last pivot
+    // step published (column j sits in warp j mod W, slot j / W): one warp
+    // converts them, one FP64 conversion per 32 slacks.
+    if (wid == W - 1)
+      for (int p2 = lane; p2 < nns; p2 += 32) {
+        const int j = sh.ns[p2];
+        sh.yv[sh.kr[p2]] = double(sh.objv[j % W][j / W]);
       }
-    }
     __syncthreads();
     // FP64 dot products (the FP64 unit is the scarce resource here: these two
     // are the only FP64 loops, m nsb + n nns multiply-adds in all).
@@ -849,7 +917,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     // with the FP32 basis inverse, the certificate.  Almost every LP passes
     // after the first round; one that fails gets up to two more rounds before
     // it goes to the FP64 re-solve.
-    const double tol = P.feas_tol, tp = tol * (1.0 + bmax), td = tol * (1.0 + cmax);
+    const double tol = P.feas_tol, tp = sh.tpd[0], td = sh.tpd[1];
     constexpr float kDeltaErr = 1.f / 32768.f;
     int fail = 0;
     for (int round = 0;; ++round) {
@@ -905,10 +973,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
         const int c = lane / (32 / CP);
         if (lane % (32 / CP) == 0 && c < C && (c < C - 1 || wid < W - 1)) {
           const int v = sh.nonb[wid + W * c];
-          if (v >= n && v < n + m) {
-            sh.yv[v - n] += double(tot);
-            sh.dyf[v - n] = tot;
-          }
+          if (v >= n && v < n + m) sh.dyf[v - n] = tot;
         }
       }
       __syncthreads();
@@ -919,8 +984,11 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
         const int v = sh.basic[t];
         const double dx = v >= n ? double(s) + sh.rr[v - n] : double(s);
         sh.xb[t] += dx;
-        sh.dxf[t] = v < n ? float(dx) : 0.f;         // the structural part of the correction
+        sh.dxf[t] = v < n ? s : 0.f;         // the structural part of the correction (double(s) exactly)
       }
+      if (wid == W - 1)                      // y += dy on the non-basic slacks, by one warp
+        for (int p2 = lane; p2 < nns; p2 += 32) sh.yv[sh.kr[p2]] += double(sh.dyf[sh.kr[p2]]);
+      if (tid == claimer && round == 0) stage3();
       __syncthreads();
       // KKT certificate of the pair that is written out (x: the structural part
       // of x_B; y: the slack duals): x >= 0, A x <= b, y >= 0, A^T y >= c and
@@ -953,11 +1021,14 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
         by = warp_sum(by);
         if (lane == 0) sh.red[1][0] = by;
       }
-      fail = __syncthreads_or(fail);
-      {
-        const double cx = sh.red[0][0], by = sh.red[1][0];
-        fail |= !(fabs(cx - by) <= tol * (1.0 + fabs(cx)));    // the duality gap (same value in every thread)
+      if (wid < 2) {         // warps 0 and 1 meet; thread 0 checks the duality gap
+        asm volatile("bar.sync 1, 64;\n" ::: "memory");
+        if (tid == 0) {
+          const double cx = sh.red[0][0], by = sh.red[1][0];
+          fail |= !(fabs(cx - by) <= tol * (1.0 + fabs(cx)));
+        }
       }
+      fail = __syncthreads_or(fail);
       if (!fail || round == 2) break;
       __syncthreads();       // sh.red and the check inputs are rewritten by the next round
     }

@@ -754,14 +754,20 @@ __device__ __forceinline__ bool refine_and_verify(const Tab<float> &S_, const Ba
       }
       dj[j] = d;
     }
-    if (np > 0.0) atomicMax(&s_nrm[0], static_cast<unsigned long long>(__double_as_longlong(np)));
+    {
+      const unsigned long long w = warp_max_u64(static_cast<unsigned long long>(__double_as_longlong(np)));
+      if (lane == 0 && w > 0ull) atomicMax(&s_nrm[0], w);
+    }
     __syncthreads();
     for (int q = tid; q < nsb; q += nt) {      // dual residual c_B - B^T y on the basic structurals
       const double r = -dj[jq[q]];
       rho[sb[q]] = r;
       nd = fmax(nd, fabs(r));
     }
-    if (nd > 0.0) atomicMax(&s_nrm[1], static_cast<unsigned long long>(__double_as_longlong(nd)));
+    {
+      const unsigned long long w = warp_max_u64(static_cast<unsigned long long>(__double_as_longlong(nd)));
+      if (lane == 0 && w > 0ull) atomicMax(&s_nrm[1], w);
+    }
     __syncthreads();
     const double rp_ = __longlong_as_double(static_cast<long long>(s_nrm[0]));
     const double rd_ = __longlong_as_double(static_cast<long long>(s_nrm[1]));
@@ -883,8 +889,14 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
     for (int j = tid; j < n; j += nt) cm = fmax(cm, fabs(ld_in(P.B.c, coff + j, P.B.dtype)));
     kneg = warp_sum(kneg);
     if ((tid & 31) == 0) atomicAdd(&s_k, kneg);
-    if (bm == bm) atomicMax(&s_bmax, static_cast<unsigned long long>(__double_as_longlong(bm)));
-    if (cm == cm) atomicMax(&s_cmax, static_cast<unsigned long long>(__double_as_longlong(cm)));
+    {
+      const unsigned long long wb = warp_max_u64(static_cast<unsigned long long>(__double_as_longlong(bm)));
+      const unsigned long long wc = warp_max_u64(static_cast<unsigned long long>(__double_as_longlong(cm)));
+      if ((tid & 31) == 0) {
+        atomicMax(&s_bmax, wb);
+        atomicMax(&s_cmax, wc);
+      }
+    }
     __syncthreads();
     S.m = m; S.n = n; S.k = s_k; S.nc = n + S.k; S.ld = tab_ld(n, S.k, int(sizeof(T))); S.nm = n + m;
     {
