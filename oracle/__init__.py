@@ -24,8 +24,9 @@ import numpy as np
 
 OPTIMAL, INFEASIBLE, UNBOUNDED, ITER_LIMIT, NUMERIC = 0, 1, 2, 3, 4
 # Pivot rules of Section 4.2: most negative reduced cost (LPC, Dantzig) or a random eligible
-# column (RPC; the random draw is a counter-based SplitMix64 key, see simplex_oracle.c).
-LPC, RPC = 0, 1
+# column (RPC; the random draw is a counter-based SplitMix64 key, see simplex_oracle.c); and
+# steepest-edge pricing with exact tableau weights (SE; not in the paper, see simplex_oracle.c).
+LPC, RPC, SE = 0, 1, 2
 STATUS_NAMES = {0: "optimal", 1: "infeasible", 2: "unbounded", 3: "iter_limit", 4: "numeric"}
 
 # Tolerances of the FP64 oracle (the paper states none): absolute, on data of order 1.

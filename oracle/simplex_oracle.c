@@ -32,7 +32,15 @@
  *     at pivot `it` of LP `lp` is the upper 32 bits of the first output of
  *     SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) started from the state
  *     seed ^ (lp << 40) ^ (it << 20) ^ j.  The random draw is thus a
- *     counter-based function of the LP, the pivot and the variable.
+ *     counter-based function of the LP, the pivot and the variable.  Under
+ *     steepest-edge pricing (the paper has only LPC and RPC; this is the
+ *     textbook rule of Goldfarb and Reid, Math. Programming 12, 1977, with the
+ *     exact weights of the tableau) the entering column maximizes
+ *     r_j^2 / gamma_j, gamma_j = 1 + sum_i t_ij^2 over the constraint rows in
+ *     use: the squared length of the edge the pivot moves along, in the space
+ *     of all variables (the entering variable moves by 1, the basic variable
+ *     of row i by -t_ij).  The sum runs over the rows in order with one fused
+ *     multiply-add per row; ties go to the lowest variable index.
  *   - Step 2 (leaving): among rows with pivot-column entry t_ie > eps_p, the
  *     minimum ratio b_i / t_ie.  Ties go to the lowest basic-variable index.
  *     No eligible row: unbounded.
@@ -73,9 +81,9 @@ typedef struct {
 
 #define TE(t, i, j) ((t)->T[(size_t)(i) * (t)->ld + (j)])
 
-enum { OR_RULE_LPC = 0, OR_RULE_RPC = 1 };
+enum { OR_RULE_LPC = 0, OR_RULE_RPC = 1, OR_RULE_SE = 2 };
 typedef struct {
-  int rule;              /* OR_RULE_LPC or OR_RULE_RPC */
+  int rule;              /* OR_RULE_LPC, OR_RULE_RPC or OR_RULE_SE */
   uint64_t seed;         /* RPC: generator seed */
   uint64_t lp;           /* RPC: index of the LP in its batch */
 } pivot_rule;
@@ -93,6 +101,17 @@ uint64_t oracle_splitmix64_next(uint64_t *state) {
 static uint32_t rpc_key(const pivot_rule *pr, uint64_t it, uint64_t j) {
   uint64_t st = pr->seed ^ (pr->lp << 40) ^ (it << 20) ^ j;
   return (uint32_t)(oracle_splitmix64_next(&st) >> 32);
+}
+
+/* Steepest-edge weight of column j: 1 + sum of t_ij^2 over the constraint
+ * rows in use, in row order. */
+static double se_weight(const tableau *t, int j) {
+  double g = 1.0;
+  for (int i = 0; i < t->m; ++i) {
+    if (t->dropped[i]) continue;
+    g = fma(TE(t, i, j), TE(t, i, j), g);
+  }
+  return g;
 }
 
 /* Step 3: pivot on (l, e). */
@@ -128,6 +147,9 @@ static int entering(const tableau *t, int orow, double eps_d, int bland, const p
     if (pr->rule == OR_RULE_RPC) {        /* smallest (key, j): j increases, so ties keep the lower j */
       const uint32_t key = rpc_key(pr, (uint64_t)it, (uint64_t)j);
       if (best < 0 || key < bk) { best = j; bk = key; }
+    } else if (pr->rule == OR_RULE_SE) {  /* largest r_j^2 / gamma_j; ties keep the lower j */
+      const double score = (r * r) / se_weight(t, j);
+      if (best < 0 || score > bv) { best = j; bv = score; }
     } else if (best < 0 || r < bv) {
       best = j; bv = r;
     }
@@ -300,8 +322,8 @@ int oracle_solve_one(int m, int n, const double *A, const double *b, const doubl
                         cert, &pr);
 }
 
-/* oracle_solve_one under pivot rule `rule` (OR_RULE_LPC or OR_RULE_RPC with
- * generator seed `seed`; `lp` is the LP's index in its batch). */
+/* oracle_solve_one under pivot rule `rule` (OR_RULE_LPC, OR_RULE_RPC with
+ * generator seed `seed`, or OR_RULE_SE; `lp` is the LP's index in its batch). */
 int oracle_solve_one_rule(int m, int n, const double *A, const double *b, const double *c,
                           int max_iter, double eps_p, double eps_d, double feas_tol,
                           double *x, double *y, double *obj, int *basis_out, int *iters_out,
