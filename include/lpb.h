@@ -121,9 +121,18 @@ typedef struct {
  *     seed ^ (k << 40) ^ (t << 20) ^ j.  The draw is a function of (seed, k, t,
  *     j) only, so FP64 solves repeat exactly; the FP32 register kernel ranks
  *     eligible columns by the upper 31 bits of the same key.
- * Under either rule, m + n consecutive degenerate pivots switch Step 1 to the
+ *   LPB_PIVOT_STEEPEST: steepest-edge pricing (not one of the paper's rules;
+ *     Goldfarb and Reid's, with exact weights read off the tableau): the
+ *     eligible column j with the largest r_j^2 / gamma_j, where gamma_j = 1 +
+ *     sum_i t_ij^2 over the constraint rows in use (rows left with an
+ *     artificial basic variable after Phase I are not), ties to the lowest
+ *     variable index.  The weights are recomputed from the tableau before
+ *     every pivot: O(m n) more work per pivot for fewer pivots.  It runs in the
+ *     shared-memory / L2-slot kernel only; LPB_KERNEL_REG with it is
+ *     LPB_EUNSUPPORTED.
+ * Under every rule, m + n consecutive degenerate pivots switch Step 1 to the
  * lowest eligible variable index (Bland's rule) until a pivot makes progress. */
-typedef enum { LPB_PIVOT_LPC = 0, LPB_PIVOT_RPC = 1 } lpb_pivot_rule;
+typedef enum { LPB_PIVOT_LPC = 0, LPB_PIVOT_RPC = 1, LPB_PIVOT_STEEPEST = 2 } lpb_pivot_rule;
 
 typedef enum {
   LPB_KERNEL_AUTO = 0,

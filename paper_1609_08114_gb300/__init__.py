@@ -28,7 +28,7 @@ __all__ = ["Solver", "LPBatch", "SolveResult", "LPBError", "OPTIMAL", "INFEASIBL
 
 PRECISIONS = {"fp64": FP64, "fp32_refine": FP32_REFINE, "fp32": FP32}
 # Step 1 rules of Section 4.2: most negative reduced cost, or a random eligible column.
-PIVOT_RULES = {"lpc": _lib.PIVOT_LPC, "rpc": _lib.PIVOT_RPC}
+PIVOT_RULES = {"lpc": _lib.PIVOT_LPC, "rpc": _lib.PIVOT_RPC, "steepest": _lib.PIVOT_STEEPEST}
 
 
 def _ptr(t):

@@ -23,7 +23,7 @@ DTYPE_F32, DTYPE_F64 = 0, 1
 # lpb_kernel
 KERNEL_AUTO, KERNEL_SMEM, KERNEL_GMEM, KERNEL_REG = 0, 1, 2, 3
 # lpb_pivot_rule
-PIVOT_LPC, PIVOT_RPC = 0, 1
+PIVOT_LPC, PIVOT_RPC, PIVOT_STEEPEST = 0, 1, 2
 
 P = ctypes.c_void_p
 

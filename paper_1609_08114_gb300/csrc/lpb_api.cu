@@ -181,7 +181,12 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   if (b->dtype != LPB_DTYPE_F32 && b->dtype != LPB_DTYPE_F64) return LPB_EINVAL;
   if (o->prec < LPB_FP64 || o->prec > LPB_FP32) return LPB_EINVAL;
   if (o->max_iter < 0 || o->eps_p < 0 || o->eps_d < 0 || o->feas_tol < 0) return LPB_EINVAL;
-  if (o->pivot_rule != LPB_PIVOT_LPC && o->pivot_rule != LPB_PIVOT_RPC) return LPB_EINVAL;
+  if (o->pivot_rule != LPB_PIVOT_LPC && o->pivot_rule != LPB_PIVOT_RPC && o->pivot_rule != LPB_PIVOT_STEEPEST)
+    return LPB_EINVAL;
+  // Steepest-edge weights are column sums over all rows: the register kernel,
+  // whose Step 1 sees one warp's columns, does not implement them.
+  const bool se = o->pivot_rule == LPB_PIVOT_STEEPEST;
+  if (se && o->kernel == LPB_KERNEL_REG) return LPB_EUNSUPPORTED;
   const bool fp32 = o->prec != LPB_FP64;
   pl->eps_p = o->eps_p > 0 ? o->eps_p : (fp32 ? 1e-6 : 1e-9);
   pl->eps_d = o->eps_d > 0 ? o->eps_d : (fp32 ? 1e-6 : 1e-9);
@@ -193,7 +198,7 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   lpb_options og = *o;          // options of the shared-memory / L2-slot kernel passes
   if (og.kernel == LPB_KERNEL_REG) { og.kernel = LPB_KERNEL_AUTO; og.threads = 0; }
   int np = 0;
-  if (fp32 && o->kernel == LPB_KERNEL_AUTO) {
+  if (fp32 && o->kernel == LPB_KERNEL_AUTO && !se) {
     // Size classes: the register-tableau templates with `want_w` warps in
     // increasing size, then the shared-memory / L2-slot kernel for the rest.
     Pass regp[kMaxClasses];
@@ -528,7 +533,7 @@ __global__ void fill_shared_meta(int32_t *m, int32_t *n, int64_t *a_off, int64_t
 lpb_options shared_options(const lpb_options *o, int m, int n) {
   lpb_options os = *o;
   if (o->prec != LPB_FP64 && o->kernel == LPB_KERNEL_AUTO && o->threads == 0 &&
-      reg_pick(m, n, o->reg_warps > 0 ? o->reg_warps : 8) >= 0)
+      o->pivot_rule != LPB_PIVOT_STEEPEST && reg_pick(m, n, o->reg_warps > 0 ? o->reg_warps : 8) >= 0)
     os.kernel = LPB_KERNEL_REG;
   return os;
 }
@@ -772,7 +777,8 @@ lpb_err lpb_solve(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const
   DeviceScope ds(h->device);
   if (!ds.ok()) return LPB_ECUDA;
   lpb_options tuned_opt;
-  if (o->kernel == LPB_KERNEL_AUTO && o->threads == 0 && o->reg_warps == 0)
+  if (o->kernel == LPB_KERNEL_AUTO && o->threads == 0 && o->reg_warps == 0 &&
+      o->pivot_rule != LPB_PIVOT_STEEPEST)     // tuned kernels may be register kernels
     for (const auto &t : h->tuned)
       if (t.max_m == b->max_m && t.max_n == b->max_n && t.dtype == b->dtype && t.prec == o->prec) {
         tuned_opt = *o;

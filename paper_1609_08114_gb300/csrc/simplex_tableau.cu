@@ -252,12 +252,35 @@ __device__ __forceinline__ void pivot(const Tab<T> &S_, int rows, int l, int e) 
   __syncthreads();
 }
 
+// Steepest-edge weights gamma_j = 1 + sum_i t_ij^2 of the columns eligible on
+// objective row `orow` (r_j < -eps_d, not artificial), summed over the
+// constraint rows in row order with one fused multiply-add each (phase 2
+// skips rows whose basic variable is artificial: redundant rows left after
+// Phase I), into S.rowb, which is free between pivots.  Every thread takes
+// columns; the caller places a barrier before (rows final) and after.
+template <typename T>
+__device__ __forceinline__ void se_weights(const Tab<T> &S_, int orow, int phase, T eps_d) {
+  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
+  const T *r = S.row(orow);
+  for (int j = threadIdx.x; j < S.nc; j += blockDim.x) {
+    if (S.nonb[j] >= S.nm || !(r[j] < -eps_d)) continue;
+    T g = T(1);
+    for (int i = 0; i < S.m; ++i) {
+      if (phase == 2 && S.basic[i] >= S.nm) continue;
+      const T t = S.at(i, j);
+      g = fma(t, t, g);
+    }
+    S.rowb[j] = g;
+  }
+}
+
 // Step 1 over objective row `orow` in one warp (every lane gets the result):
 // eligible columns are those with a reduced cost below -eps_d; the most
 // negative one enters (LPC), or the one with the smallest random key at pivot
-// `it` (RPC), or the lowest variable index under Bland's rule.  Column `ecol`
-// is taken to hold variable `evar` (a pivot whose swap of nonb may not be
-// visible yet).  Keys are (variable << kIdxBits) | column.
+// `it` (RPC), or the one with the largest r_j^2 / gamma_j (steepest edge, the
+// weights in S.rowb), or the lowest variable index under Bland's rule.  Column
+// `ecol` is taken to hold variable `evar` (a pivot whose swap of nonb may not
+// be visible yet).  Keys are (variable << kIdxBits) | column.
 template <typename T>
 __device__ __forceinline__ void step1_warp(const Tab<T> &S_, int orow, bool bland, T eps_d, int ecol, int evar,
                                            T &v, int &key, int rule, unsigned long long seed, long long lp,
@@ -278,6 +301,37 @@ __device__ __forceinline__ void step1_warp(const Tab<T> &S_, int orow, bool blan
     const unsigned mk = __reduce_min_sync(kFull, best);
     key = int(__reduce_min_sync(kFull, best == mk ? unsigned(key) : 0xffffffffu));   // INT_MAX if none
     v = T(0);
+    return;
+  }
+  if (rule == LPB_PIVOT_STEEPEST && !bland) {
+    // The value is -r_j^2 / gamma_j.  In FP64 the quotients are first formed
+    // in FP32 (relative error below 4e-7; FP64 division is slow here) and only
+    // columns within 1e-5 of the largest FP32 score get the exact one, which
+    // keeps the exact maximum and its ties among them.
+    float cut = 0.f;
+    if constexpr (sizeof(T) == 8) {
+      float b32 = 0.f;
+      for (int j = threadIdx.x & 31; j < S.nc; j += 32) {
+        const int var = j == ecol ? evar : S.nonb[j];
+        if (var >= S.nm || !(r[j] < -eps_d)) continue;
+        const float r32 = d2f_rn(r[j]);
+        b32 = fmaxf(b32, __fdiv_rn(r32 * r32, d2f_rn(S.rowb[j])));
+      }
+      b32 = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(b32)));   // >= 0: bits order like values
+      cut = isfinite(b32) ? b32 * (1.f - 1e-5f) : 0.f;
+    }
+    for (int j = threadIdx.x & 31; j < S.nc; j += 32) {
+      const int var = j == ecol ? evar : S.nonb[j];
+      if (var >= S.nm) continue;
+      const T rj = r[j];
+      if (!(rj < -eps_d)) continue;
+      if constexpr (sizeof(T) == 8) {
+        const float r32 = d2f_rn(rj);
+        if (__fdiv_rn(r32 * r32, d2f_rn(S.rowb[j])) < cut) continue;
+      }
+      keep_better(v, key, -((rj * rj) / S.rowb[j]), (var << kIdxBits) | j);
+    }
+    warp_argmin(v, key);
     return;
   }
   for (int j = threadIdx.x & 31; j < S.nc; j += 32) {
@@ -301,8 +355,15 @@ __device__ __forceinline__ int run_phase(const Tab<T> &S_, int orow, int rows, i
   own_rows(rows, r0, r1);
   const int per = (rows + nw - 1) / nw;
   const bool obj_warp = orow >= r0 && orow < r1;
+  // Steepest edge needs every row of the updated tableau for its weights, so
+  // its Step 1 follows the pivot's last barrier instead of overlapping it.
+  const bool se = rule == LPB_PIVOT_STEEPEST;
   int degenerate_run = 0;
   bool bland = false;
+  if (se) {
+    se_weights(S, orow, phase, eps_d);
+    __syncthreads();
+  }
   if (w == 0) {            // Step 1 of the first pivot
     T v;
     int key;
@@ -391,7 +452,7 @@ __device__ __forceinline__ int run_phase(const Tab<T> &S_, int orow, int rows, i
       degenerate_run = 0;
       bland = false;
     }
-    if (obj_warp) {        // Step 1 of the next pivot on the updated objective row
+    if (obj_warp && !se) {   // Step 1 of the next pivot on the updated objective row
       __syncwarp();
       T v;
       int key;
@@ -400,6 +461,18 @@ __device__ __forceinline__ int run_phase(const Tab<T> &S_, int orow, int rows, i
     }
     __syncthreads();
     pivot_finish(S, rows, l);
+    if (se) {
+      __syncthreads();       // the pivot row is in place
+      se_weights(S, orow, phase, eps_d);
+      __syncthreads();
+      if (w == 0) {
+        T v;
+        int key;
+        step1_warp(S, orow, bland, eps_d, -1, 0, v, key, rule, seed, lp, iters);
+        if (lane == 0) S.sel[0] = key;
+      }
+      __syncthreads();
+    }
   }
 }
 
