@@ -410,8 +410,7 @@ def secondary_legs(solver, dev):
     bt = _type1_device(50_000, 100, 100, dev, seed=100)
     solve_leg("type1_50000x100_lpc", bt, reps=3)
     solve_leg("type1_50000x100_rpc", bt, reps=3, pivot_rule="rpc", seed=1)
-    # steepest-edge pricing (not in the paper): fewer pivots, O(mn) weights per pivot,
-    # shared-memory / L2-slot kernel only
+    # steepest-edge pricing (not in the paper): fewer pivots, O(mn) weights per pivot
     solve_leg("type1_50000x100_steepest", bt, reps=3, pivot_rule="steepest")
     del bt
     torch.cuda.empty_cache()

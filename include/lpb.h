@@ -127,9 +127,9 @@ typedef struct {
  *     sum_i t_ij^2 over the constraint rows in use (rows left with an
  *     artificial basic variable after Phase I are not), ties to the lowest
  *     variable index.  The weights are recomputed from the tableau before
- *     every pivot: O(m n) more work per pivot for fewer pivots.  It runs in the
- *     shared-memory / L2-slot kernel only; LPB_KERNEL_REG with it is
- *     LPB_EUNSUPPORTED.
+ *     every pivot: O(m n) more work per pivot for fewer pivots.  The register
+ *     kernel has it in its 8-warp templates only: LPB_KERNEL_REG with
+ *     reg_warps = 4 and this rule is LPB_EUNSUPPORTED.
  * Under every rule, m + n consecutive degenerate pivots switch Step 1 to the
  * lowest eligible variable index (Bland's rule) until a pivot makes progress. */
 typedef enum { LPB_PIVOT_LPC = 0, LPB_PIVOT_RPC = 1, LPB_PIVOT_STEEPEST = 2 } lpb_pivot_rule;

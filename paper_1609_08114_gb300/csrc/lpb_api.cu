@@ -159,9 +159,11 @@ lpb_err make_pass(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   return LPB_OK;
 }
 
-lpb_err reg_pass(const DeviceInfo &d, const lpb_batch *b, int cfg, int lim_m, int lim_n, int mode, Pass *p) {
+lpb_err reg_pass(const DeviceInfo &d, const lpb_batch *b, int cfg, int lim_m, int lim_n, int mode, int rule,
+                 Pass *p) {
   int occ = 0;
-  if (reg_occupancy(cfg, lim_m, lim_n, b->dtype, &occ, &p->threads, &p->smem) != cudaSuccess) return LPB_ECUDA;
+  if (reg_occupancy(cfg, lim_m, lim_n, b->dtype, rule, &occ, &p->threads, &p->smem) != cudaSuccess)
+    return LPB_ECUDA;
   if (p->smem > d.smem_optin || occ < 1) return LPB_EUNSUPPORTED;   // the input does not fit on chip
   p->fp64 = false;
   p->mode = mode;
@@ -183,10 +185,8 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   if (o->max_iter < 0 || o->eps_p < 0 || o->eps_d < 0 || o->feas_tol < 0) return LPB_EINVAL;
   if (o->pivot_rule != LPB_PIVOT_LPC && o->pivot_rule != LPB_PIVOT_RPC && o->pivot_rule != LPB_PIVOT_STEEPEST)
     return LPB_EINVAL;
-  // Steepest-edge weights are column sums over all rows: the register kernel,
-  // whose Step 1 sees one warp's columns, does not implement them.
+  // Steepest edge has register-kernel instantiations for the 8-warp templates only.
   const bool se = o->pivot_rule == LPB_PIVOT_STEEPEST;
-  if (se && o->kernel == LPB_KERNEL_REG) return LPB_EUNSUPPORTED;
   const bool fp32 = o->prec != LPB_FP64;
   pl->eps_p = o->eps_p > 0 ? o->eps_p : (fp32 ? 1e-6 : 1e-9);
   pl->eps_d = o->eps_d > 0 ? o->eps_d : (fp32 ? 1e-6 : 1e-9);
@@ -198,7 +198,7 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   lpb_options og = *o;          // options of the shared-memory / L2-slot kernel passes
   if (og.kernel == LPB_KERNEL_REG) { og.kernel = LPB_KERNEL_AUTO; og.threads = 0; }
   int np = 0;
-  if (fp32 && o->kernel == LPB_KERNEL_AUTO && !se) {
+  if (fp32 && o->kernel == LPB_KERNEL_AUTO) {
     // Size classes: the register-tableau templates with `want_w` warps in
     // increasing size, then the shared-memory / L2-slot kernel for the rest.
     Pass regp[kMaxClasses];
@@ -208,7 +208,7 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
     for (int i = 0; i < reg_count() && cnt < 16; ++i) {
       int mm, nn, ww;
       reg_limits(i, &mm, &nn, &ww);
-      if (ww == want_w) order[cnt++] = i;
+      if (ww == want_w && (!se || reg_has_se(i))) order[cnt++] = i;
     }
     for (int a = 0; a < cnt; ++a)        // by capacity, smallest first
       for (int c = a + 1; c < cnt; ++c) {
@@ -223,7 +223,7 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
       const int lm = mm < b->max_m ? mm : b->max_m, ln = nn < b->max_n ? nn : b->max_n;
       if (nreg > 0 && lm <= pl->cls_m[nreg - 1] && ln <= pl->cls_n[nreg - 1]) continue;
       Pass p;
-      if (reg_pass(d, b, order[a], lm, ln, mode, &p) != LPB_OK) continue;
+      if (reg_pass(d, b, order[a], lm, ln, mode, o->pivot_rule, &p) != LPB_OK) continue;
       p.list = LIST_CLASS;
       p.cls = nreg;
       pl->cls_m[nreg] = lm;
@@ -250,10 +250,10 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   }
   if (np == 0) {                   // one first pass over every LP
     Pass &p = pl->pass[0];
-    const int reg = (fp32 && o->kernel == LPB_KERNEL_REG) ? reg_pick(b->max_m, b->max_n, want_w) : -1;
+    const int reg = (fp32 && o->kernel == LPB_KERNEL_REG) ? reg_pick(b->max_m, b->max_n, want_w, se) : -1;
     if (o->kernel == LPB_KERNEL_REG && reg < 0) return LPB_EUNSUPPORTED;
     if (reg >= 0) {
-      if ((e = reg_pass(d, b, reg, b->max_m, b->max_n, mode, &p)) != LPB_OK) return e;
+      if ((e = reg_pass(d, b, reg, b->max_m, b->max_n, mode, o->pivot_rule, &p)) != LPB_OK) return e;
     } else if ((e = make_pass(d, b, &og, !fp32, 0, mode, &p)) != LPB_OK) {
       return e;
     }
@@ -533,7 +533,7 @@ __global__ void fill_shared_meta(int32_t *m, int32_t *n, int64_t *a_off, int64_t
 lpb_options shared_options(const lpb_options *o, int m, int n) {
   lpb_options os = *o;
   if (o->prec != LPB_FP64 && o->kernel == LPB_KERNEL_AUTO && o->threads == 0 &&
-      o->pivot_rule != LPB_PIVOT_STEEPEST && reg_pick(m, n, o->reg_warps > 0 ? o->reg_warps : 8) >= 0)
+      reg_pick(m, n, o->reg_warps > 0 ? o->reg_warps : 8, o->pivot_rule == LPB_PIVOT_STEEPEST) >= 0)
     os.kernel = LPB_KERNEL_REG;
   return os;
 }
@@ -778,7 +778,7 @@ lpb_err lpb_solve(lpb_handle *h, const lpb_batch *b, const lpb_options *o, const
   if (!ds.ok()) return LPB_ECUDA;
   lpb_options tuned_opt;
   if (o->kernel == LPB_KERNEL_AUTO && o->threads == 0 && o->reg_warps == 0 &&
-      o->pivot_rule != LPB_PIVOT_STEEPEST)     // tuned kernels may be register kernels
+      o->pivot_rule != LPB_PIVOT_STEEPEST)     // tuned register kernels may lack a steepest-edge instantiation
     for (const auto &t : h->tuned)
       if (t.max_m == b->max_m && t.max_n == b->max_n && t.dtype == b->dtype && t.prec == o->prec) {
         tuned_opt = *o;

@@ -308,10 +308,11 @@ cudaError_t launch_tableau(const TableauParams &p, bool fp64, int grid, int thre
 // defer list every LP it does not take (Phase I, sizes, non-finite data).
 size_t classify_hist_bytes(int nclass);
 cudaError_t launch_classify(const ClassPlanParams &p, int sms, cudaStream_t s);
-int reg_pick(int max_m, int max_n, int want_warps);
+int reg_pick(int max_m, int max_n, int want_warps, bool se = false);
+bool reg_has_se(int cfg);
 int reg_count();
 void reg_limits(int cfg, int *max_m, int *max_n, int *warps);
-cudaError_t reg_occupancy(int cfg, int max_m, int max_n, int dtype, int *ctas, int *threads, size_t *smem);
+cudaError_t reg_occupancy(int cfg, int max_m, int max_n, int dtype, int rule, int *ctas, int *threads, size_t *smem);
 cudaError_t launch_reg(const TableauParams &p, int cfg, int grid, size_t smem, cudaStream_t s);
 size_t hyperbox_smem_bytes(int n, int elem_bytes, bool shared_box);
 cudaError_t launch_hyperbox(const HyperboxParams &p, uint32_t *err, cudaStream_t s);

@@ -251,7 +251,38 @@ __device__ __forceinline__ double a_at(const unsigned char *sa, int dt, int idx)
 template <int R, int C, int W>
 constexpr int reg_min_blocks() { return R * C <= 8 ? (W <= 4 ? 4 : 3) : (R == 4 && W <= 4) ? 2 : (W <= 4 ? 3 : 2); }
 
-template <int R, int C, int W>
+// Steepest-edge weight gamma_c = 1 + sum_i t_ic^2 of this warp's column
+// wid + W lane, for lanes c < C, over the constraint rows (every row but the
+// objective row, lane 31's row R-1; padding rows are zero).  Columns go four
+// at a time through a reduce-scatter, so few registers are live.
+template <int R, int C>
+__device__ __forceinline__ float se_gamma(const float (&T)[R][C], int lane) {
+  const float keep_last = lane == 31 ? 0.f : 1.f;
+  float g = 0.f;
+#pragma unroll
+  for (int c0 = 0; c0 < C; c0 += 4) {
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float s = 0.f;
+      if (c0 + k < C) {
+#pragma unroll
+        for (int r = 0; r < R - 1; ++r) s = fmaf(T[r][c0 + k], T[r][c0 + k], s);
+        const float t = T[R - 1][c0 + k] * keep_last;
+        s = fmaf(t, t, s);
+      }
+      v[k] = s;
+    }
+    const float tot = reduce_scatter<4>(v, lane);            // lane l: column c0 + l / 8
+    const float mine = __shfl_sync(kFull, tot, ((lane - c0) & 3) * 8);
+    if (lane >= c0 && lane < c0 + 4) g = mine;
+  }
+  return 1.f + g;
+}
+
+// SE: steepest-edge pricing in Step 1 (a separate instantiation, so that the
+// other rules' kernels carry none of its registers or instructions).
+template <int R, int C, int W, bool SE>
 __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(TableauParams P) {
   using SH = RegShared<R, C, W>;
   constexpr int ROWS = SH::ROWS, COLS = SH::COLS;
@@ -614,6 +645,10 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       __syncwarp();
       float cv = __int_as_float(0x7f800000);
       int ck = kBad;
+      float gam = 1.f;
+      if constexpr (SE) {
+        if (!bland) gam = se_gamma<R, C>(T, lane);
+      }
       {
         const int j = wid + W * lane;
         if (lane < C && j < COLS - 1) {                // the last column is the right-hand side
@@ -622,7 +657,8 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
             // The random rule ranks by the upper 31 bits of the variable's key,
             // stored as the bits of a non-negative float: the arg-min compares
             // the order-preserving integer image, never the float value.
-            cv = bland ? 0.f : P.rule == LPB_PIVOT_RPC ? __uint_as_float(rpc_key(P.seed, P.lp_base + lp, iters, nvar) >> 1) : rj;
+            if constexpr (SE) cv = bland ? 0.f : -__fdiv_rn(rj * rj, gam);     // the largest r_j^2 / gamma_j
+            else cv = bland ? 0.f : P.rule == LPB_PIVOT_RPC ? __uint_as_float(rpc_key(P.seed, P.lp_base + lp, iters, nvar) >> 1) : rj;
             ck = (nvar << kIdxBits) | j;
           }
         }
@@ -1056,16 +1092,21 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
 struct RegConfig {
   int R, C, W;
   const void *fn;
+  const void *fn_se;     // the steepest-edge instantiation, or null
   size_t fixed;
 };
 
 #define LPB_REG(R, C, W) \
-  RegConfig{R, C, W, reinterpret_cast<const void *>(&reg_kernel<R, C, W>), reg_fixed_bytes<R, C, W>()}
+  RegConfig{R, C, W, reinterpret_cast<const void *>(&reg_kernel<R, C, W, false>), nullptr, reg_fixed_bytes<R, C, W>()}
+#define LPB_REG_SE(R, C, W)                                                                         \
+  RegConfig{R, C, W, reinterpret_cast<const void *>(&reg_kernel<R, C, W, false>),                   \
+            reinterpret_cast<const void *>(&reg_kernel<R, C, W, true>), reg_fixed_bytes<R, C, W>()}
 const RegConfig kRegConfigs[] = {
     LPB_REG(1, 8, 4), LPB_REG(2, 16, 4), LPB_REG(4, 26, 4), LPB_REG(4, 32, 4),
-    LPB_REG(1, 4, 8), LPB_REG(2, 8, 8), LPB_REG(4, 13, 8), LPB_REG(4, 16, 8),
+    LPB_REG_SE(1, 4, 8), LPB_REG_SE(2, 8, 8), LPB_REG_SE(4, 13, 8), LPB_REG_SE(4, 16, 8),
 };
 #undef LPB_REG
+#undef LPB_REG_SE
 constexpr int kNumReg = int(sizeof(kRegConfigs) / sizeof(kRegConfigs[0]));
 
 size_t reg_smem_bytes(int cfg, int max_m, int max_n, int dtype) {
@@ -1085,36 +1126,44 @@ void reg_limits(int cfg, int *max_m, int *max_n, int *warps) {
   *warps = k.W;
 }
 
+// Whether configuration `cfg` has a steepest-edge instantiation (the 8-warp ones).
+bool reg_has_se(int cfg) { return kRegConfigs[cfg].fn_se != nullptr; }
+
 // Smallest configuration whose rows hold max_m + 1 and columns max_n + 1,
-// with `want_w` warps when given (8 warps by default); -1 if none fits.
-int reg_pick(int max_m, int max_n, int want_w) {
+// with `want_w` warps when given (8 warps by default) and, when `se`, a
+// steepest-edge instantiation; -1 if none fits.
+int reg_pick(int max_m, int max_n, int want_w, bool se) {
   if (want_w <= 0) want_w = 8;
   int best = -1, best_cost = 1 << 30;
   for (int i = 0; i < kNumReg; ++i) {
     const RegConfig &k = kRegConfigs[i];
-    if (32 * k.R - 1 < max_m || k.W * k.C - 1 < max_n || k.W != want_w) continue;
+    if (32 * k.R - 1 < max_m || k.W * k.C - 1 < max_n || k.W != want_w || (se && !k.fn_se)) continue;
     const int cost = k.R * k.C * k.W;
     if (cost < best_cost) { best_cost = cost; best = i; }
   }
   return best;
 }
 
-cudaError_t reg_occupancy(int cfg, int max_m, int max_n, int dtype, int *ctas, int *threads,
+cudaError_t reg_occupancy(int cfg, int max_m, int max_n, int dtype, int rule, int *ctas, int *threads,
                           size_t *smem) {
   const RegConfig &k = kRegConfigs[cfg];
+  const void *fn = rule == LPB_PIVOT_STEEPEST ? k.fn_se : k.fn;
+  if (!fn) return cudaErrorInvalidValue;
   *threads = 32 * k.W;
   *smem = reg_smem_bytes(cfg, max_m, max_n, dtype);
-  cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(*smem));
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(*smem));
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, k.fn, *threads, *smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, *threads, *smem);
 }
 
 cudaError_t launch_reg(const TableauParams &p, int cfg, int grid, size_t smem, cudaStream_t s) {
   const RegConfig &k = kRegConfigs[cfg];
-  cudaError_t e = cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  const void *fn = p.rule == LPB_PIVOT_STEEPEST ? k.fn_se : k.fn;
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   void *args[] = {const_cast<TableauParams *>(&p)};
-  return cudaLaunchKernel(k.fn, dim3(grid), dim3(32 * k.W), args, smem, s);
+  return cudaLaunchKernel(fn, dim3(grid), dim3(32 * k.W), args, smem, s);
 }
 
 }  // namespace lpb

@@ -5,8 +5,8 @@ In FP64 the weights are summed in the oracle's row order and the scores compared
 (after an FP32 prefilter that keeps every candidate within 1e-5 of the best), so the GPU
 follows the oracle's pivot path up to rare near-ties that round differently: statuses
 and objectives must match and the pivot counts agree.  The FP32 + FP64-refine form must
-give the oracle's statuses and objectives to 1e-8.  The rule runs in the shared-memory /
-L2-slot kernel: a request for the register kernel is refused.
+give the oracle's statuses and objectives to 1e-8, on the shared-memory / L2-slot kernel
+and on the register kernel (its 8-warp templates; a 4-warp register request is refused).
 """
 import numpy as np
 import pytest
@@ -49,7 +49,7 @@ def test_steepest_fp64_two_phase(solver):
     assert np.mean(got["iters"] == ref["iters"]) >= 0.95
 
 
-@pytest.mark.parametrize("kernel", [0, 1, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 def test_steepest_fp32_refine(solver, kernel):
     sb = synth.type1(400, 60, 60, seed=42)
     got = _run(solver, sb, "fp32_refine", kernel=kernel)
@@ -75,8 +75,36 @@ def test_steepest_takes_fewer_pivots_on_the_gpu(solver):
     assert torch.allclose(se.obj, lpc.obj, rtol=1e-10, atol=0)
 
 
-def test_steepest_refuses_the_register_kernel(solver):
+def test_steepest_register_kernel_takes_fewer_pivots(solver):
+    sb = synth.type1(2000, 50, 50, seed=44)
+    dev = to_device(sb)
+    lpc = solver.solve(dev, prec="fp32_refine", kernel=3)
+    se = solver.solve(dev, prec="fp32_refine", kernel=3, pivot_rule="steepest")
+    torch.cuda.synchronize()
+    assert bool((se.status == 0).all()) and bool((lpc.status == 0).all())
+    assert se.iters.float().mean().item() < 0.95 * lpc.iters.float().mean().item()
+    assert torch.allclose(se.obj, lpc.obj, rtol=1e-9, atol=0)
+
+
+def test_steepest_shared_constraints_warm_start(solver):
+    """One polytope, many directions, on the register kernel's warm starts: the objectives
+    equal those of an explicit batch solved by the oracle."""
+    rng = np.random.default_rng(45)
+    m, n, k = 40, 40, 300
+    A = rng.uniform(0.1, 1.0, (m, n)); b = rng.uniform(1.0, 10.0, m)
+    C = rng.uniform(0.0, 1.0, (k, n))
+    dev = torch.device("cuda", 0)
+    r = solver.solve_shared(torch.tensor(A, device=dev), torch.tensor(b, device=dev),
+                            torch.tensor(C, device=dev), prec="fp32_refine", pivot_rule="steepest")
+    torch.cuda.synchronize()
+    ref = np.array([oracle.solve_one(A, b, C[i], rule=oracle.SE)["obj"] for i in range(k)])
+    got = r.obj.cpu().numpy()
+    assert bool((r.status == 0).all())
+    assert np.max(np.abs(got - ref) / (1 + np.abs(ref))) <= 1e-8
+
+
+def test_steepest_refuses_the_four_warp_register_kernel(solver):
     from paper_1609_08114_gb300 import LPBError
     sb = synth.type1(4, 10, 10, seed=1)
     with pytest.raises(LPBError):
-        solver.solve(to_device(sb), prec="fp32_refine", pivot_rule="steepest", kernel=3)
+        solver.solve(to_device(sb), prec="fp32_refine", pivot_rule="steepest", kernel=3, reg_warps=4)
