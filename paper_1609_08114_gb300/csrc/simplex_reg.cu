@@ -132,6 +132,7 @@ struct RegShared {
   alignas(16) float objv[W][(C + 3) & ~3];   // objective row, per warp
   RegDesc desc[2];                           // this LP's and the next one's, by LP parity
   int cstage;                                // how far the next LP's descriptor has come
+  int pre;                                   // the next LP's A, b and c are already requested
   int nsb, nns;
   int warm_ok;                               // shared constraints: start from the previous basis
   unsigned long long wbmax[W], wcmax[W];     // |b|max and |c|max bits, per warp
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
   if (tid == 0) {
     mbar_init(&sh.abar, 1);
     fence_mbar_init();
+    sh.pre = 0;
   }
   unsigned aphase = 0;        // parity of the next completion of sh.abar
   // Lane 0 of the last warp claims work items one LP ahead.  Each global round
@@ -320,6 +322,11 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       return atomicAdd(P.queue, 1) * kShareChunk;
     }
     return atomicAdd(P.queue, 1);
+  };
+  // Sizes this launch's template and limits hold (else the LP is deferred).
+  auto fits_lp = [&](int m, int n) {
+    return m >= 1 && n >= 1 && m <= ROWS - 1 && n <= COLS - 1 && m <= P.B.max_m && n <= P.B.max_n &&
+           m <= P.lim_m && n <= P.lim_n;
   };
   int next = 0;
   int slot = 0;                 // descriptor slot of the current LP (same in every thread)
@@ -384,6 +391,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     const RegDesc &D = sh.desc[slot];
     const int item = D.item;
     if (item >= nitems) break;
+    const bool pre = sh.pre != 0;          // reset by thread 0 after the next barrier
     const bool warm = sh.warm_ok != 0;     // keep the basis; load and price only the new objective
     warm_run = warm ? warm_run + 1 : 0;
     valid_tab = 0;
@@ -391,8 +399,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     const int m = D.m, n = D.n;
     const int64_t aoff = D.aoff, boff = D.boff, coff = D.coff;
     // ---- admission: sizes that fit the template, b >= 0, finite b and c ----
-    const bool fits = m >= 1 && n >= 1 && m <= ROWS - 1 && n <= COLS - 1 && m <= P.B.max_m && n <= P.B.max_n &&
-                      m <= P.lim_m && n <= P.lim_n;
+    const bool fits = fits_lp(m, n);
     const unsigned char *Ag = static_cast<const unsigned char *>(P.B.A) + aoff * es;
     // Rows of A whose global start and length are whole 16-byte units go by
     // bulk copy (the copy engine, one instruction per row); others by 4- or
@@ -414,7 +421,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     const bool bulk_bc = fits && !warm && ((reinterpret_cast<uintptr_t>(bgp) | reinterpret_cast<uintptr_t>(cgp) |
                                             uintptr_t(m) * es | uintptr_t(n) * es) & 15) == 0;
     const bool bulk_c = fits && warm && ((reinterpret_cast<uintptr_t>(cgp) | uintptr_t(n) * es) & 15) == 0;
-    if (fits) {
+    if (fits && !pre) {
       if (!bulk_bc && !bulk_c) {      // b (not on a warm start, it is resident) and c by small copies
         if (dt == LPB_DTYPE_F64) {
           const double *bg = reinterpret_cast<const double *>(bgp), *cg = reinterpret_cast<const double *>(cgp);
@@ -470,7 +477,9 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       timed_out = !mbar_wait_bounded(&sh.abar, aphase);
       aphase ^= 1u;
     }
-    if (__syncthreads_or(timed_out)) {
+    const int any_timeout = __syncthreads_or(timed_out);
+    if (tid == 0) sh.pre = 0;
+    if (any_timeout) {
       // The copy engine did not deliver the data in time: hand this LP and the one
       // claimed after it to the generic kernel, give the copies one more
       // bounded wait, and stop this CTA.
@@ -1067,6 +1076,32 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       fail = __syncthreads_or(fail);
       if (!fail || round == 2) break;
       __syncthreads();       // sh.red and the check inputs are rewritten by the next round
+    }
+    // The next LP's A, b and c, when one bulk copy each serves them: every read
+    // of this LP's copies is behind the certificate's last barrier, so the
+    // copy engine may overwrite them while this LP's results are written and
+    // the loop head runs.  (Shared-constraint batches keep A and b resident.)
+    // The last warp issues them (it has the fewest results to write): one lane
+    // sets the expected bytes, then three lanes issue one copy each.
+    if (wid == W - 1 && !P.shared) {
+      const RegDesc &N = sh.desc[slot ^ 1];
+      if (N.item < nitems && fits_lp(N.m, N.n)) {
+        const unsigned m2 = unsigned(N.m), n2 = unsigned(N.n);
+        const unsigned char *Ag2 = static_cast<const unsigned char *>(P.B.A) + N.aoff * es;
+        const unsigned char *bg2 = static_cast<const unsigned char *>(P.B.b) + N.boff * es;
+        const unsigned char *cg2 = static_cast<const unsigned char *>(P.B.c) + N.coff * es;
+        const bool dense2 = ((reinterpret_cast<uintptr_t>(Ag2) | uintptr_t(m2) * n2 * unsigned(es)) & 15) == 0;
+        const bool bc2 = ((reinterpret_cast<uintptr_t>(bg2) | reinterpret_cast<uintptr_t>(cg2) |
+                           uintptr_t(m2) * unsigned(es) | uintptr_t(n2) * unsigned(es)) & 15) == 0;
+        if (dense2 && bc2) {          // the same value in every lane
+          if (lane == 0) mbar_expect_tx(&sh.abar, m2 * n2 * unsigned(es) + (m2 + n2) * unsigned(es));
+          __syncwarp();
+          if (lane == 0) bulk_load(sA, Ag2, m2 * n2 * unsigned(es), &sh.abar);
+          else if (lane == 1) bulk_load(sh.bin, bg2, m2 * unsigned(es), &sh.abar);
+          else if (lane == 2) bulk_load(sh.cin, cg2, n2 * unsigned(es), &sh.abar);
+          if (lane == 0) sh.pre = 1;
+        }
+      }
     }
     if (fail) valid_tab = 0;            // the next objective starts cold
     if (bp) for (int i = tid; i < m; i += NT) bp[i] = sh.basic[i];
