@@ -106,7 +106,8 @@ typedef struct {
   int32_t keep_basis_inverse;/* keep what lpb_solve_backward needs in ws [0] */
   int32_t kernel;            /* lpb_kernel: force a kernel class [LPB_KERNEL_AUTO] */
   int32_t threads;           /* threads per CTA of the tableau kernel, a multiple of 32 up to 1024 [auto] */
-  int32_t reg_warps;         /* warps per LP of the register kernel, 4 or 8 [autotuned, else 8] */
+  int32_t reg_warps;         /* warps per LP of the register kernel: 1 (m, n <= 31), 4 or 8
+                                [autotuned, else 1 when every LP has m, n <= 31, else 8] */
   int32_t pivot_rule;        /* lpb_pivot_rule: Step 1's entering-column rule [LPB_PIVOT_LPC] */
   uint64_t seed;             /* LPB_PIVOT_RPC: seed of the counter-based random draw [0] */
 } lpb_options;

@@ -193,8 +193,11 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   pl->feas_tol = o->feas_tol > 0 ? o->feas_tol : 1e-9;
   lpb_err e;
   const int mode = o->prec == LPB_FP64 ? MODE_FP64 : o->prec == LPB_FP32 ? MODE_FP32 : MODE_FP32_REFINE;
+  // Warps per LP of the register templates: as asked; else one warp per LP
+  // when every LP has m, n <= 31 (many tiny LPs in flight per SM), else 8.
   const int want_w = o->reg_warps > 0 ? o->reg_warps
-                   : (o->kernel == LPB_KERNEL_REG && o->threads > 0) ? o->threads / 32 : 8;
+                   : (o->kernel == LPB_KERNEL_REG && o->threads > 0) ? o->threads / 32
+                   : (b->max_m <= 31 && b->max_n <= 31) ? 1 : 8;
   lpb_options og = *o;          // options of the shared-memory / L2-slot kernel passes
   if (og.kernel == LPB_KERNEL_REG) { og.kernel = LPB_KERNEL_AUTO; og.threads = 0; }
   int np = 0;
@@ -1057,7 +1060,8 @@ lpb_err lpb_autotune(lpb_handle *h, const lpb_batch *b, const lpb_options *o, co
   struct Cand { int kernel, threads, reg_warps; };
   const bool fp32 = o->prec != LPB_FP64;
   const Cand cands[] = {
-      {LPB_KERNEL_AUTO, 0, fp32 ? 8 : 0}, {LPB_KERNEL_AUTO, 0, fp32 ? 4 : 0}, {LPB_KERNEL_AUTO, 256, fp32 ? 8 : 0},
+      {LPB_KERNEL_AUTO, 0, fp32 ? 8 : 0}, {LPB_KERNEL_AUTO, 0, fp32 ? 4 : 0}, {LPB_KERNEL_AUTO, 0, fp32 ? 1 : 0},
+      {LPB_KERNEL_AUTO, 256, fp32 ? 8 : 0},
       {LPB_KERNEL_AUTO, 512, fp32 ? 8 : 0}, {LPB_KERNEL_AUTO, 1024, fp32 ? 8 : 0}, {LPB_KERNEL_SMEM, 0, 0},
       {LPB_KERNEL_GMEM, 0, 0}};
   cudaStream_t s = static_cast<cudaStream_t>(stream);

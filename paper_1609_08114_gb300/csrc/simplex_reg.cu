@@ -250,7 +250,9 @@ __device__ __forceinline__ double a_at(const unsigned char *sa, int dt, int idx)
 // Minimum resident CTAs per SM: more for the small tableaux, fewer for the
 // 4-warp CTAs with 128 rows, whose tableau alone takes C * 4 registers.
 template <int R, int C, int W>
-constexpr int reg_min_blocks() { return R * C <= 8 ? (W <= 4 ? 4 : 3) : (R == 4 && W <= 4) ? 2 : (W <= 4 ? 3 : 2); }
+constexpr int reg_min_blocks() {
+  return W == 1 ? 16 : R * C <= 8 ? (W <= 4 ? 4 : 3) : (R == 4 && W <= 4) ? 2 : (W <= 4 ? 3 : 2);
+}
 
 // Steepest-edge weight gamma_c = 1 + sum_i t_ic^2 of this warp's column
 // wid + W lane, for lanes c < C, over the constraint rows (every row but the
@@ -815,7 +817,9 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     // ---- FP64 refinement and certificate, with A read from shared memory ----
     // Lists: the q-th basic structural sits in row sb[q] and column jb[q] of
     // A; the p-th non-basic slack sits in tableau column ns[p] and row kr[p]
-    // of A.  Warp 0 builds the row lists, warp 1 the column lists.
+    // of A.  Warp 0 builds the row lists, warp 1 the column lists (a one-warp
+    // CTA builds both).
+    constexpr int kColWarp = W > 1 ? 1 : 0;
     if (wid == 0) {
       int base = 0;
       for (int i0 = 0; i0 < m; i0 += 32) {
@@ -831,7 +835,8 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
         base += __popc(mk);
       }
       if (lane == 0) sh.nsb = base;
-    } else if (wid == 1) {
+    }
+    if (wid == kColWarp) {
       int base = 0;
       for (int j0 = 0; j0 < COLS - 1; j0 += 32) {
         const int j = j0 + lane;
@@ -1054,20 +1059,22 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
         const float dl = col_delta(j, mag);
         fail |= !(sh.dj[j] + double(dl - kDeltaErr * mag) >= -td);
       }
-      // c^T x in warp 0 and b^T y in warp 1 (FP64).
+      // c^T x in warp 0 and b^T y in warp 1 (FP64; a one-warp CTA forms both).
       if (wid == 0) {
         double cx = 0.0;
         for (int q = lane; q < nsb; q += 32) cx = fma(vin(sh.cin, sh.jb[q], dt), sh.xb[sh.sb[q]], cx);
         cx = warp_sum(cx);
         if (lane == 0) sh.red[0][0] = cx;
-      } else if (wid == 1) {
+      }
+      if (wid == kColWarp) {
         double by = 0.0;
         for (int p2 = lane; p2 < nns; p2 += 32) by = fma(vin(sh.bin, sh.kr[p2], dt), sh.yv[sh.kr[p2]], by);
         by = warp_sum(by);
         if (lane == 0) sh.red[1][0] = by;
       }
       if (wid < 2) {         // warps 0 and 1 meet; thread 0 checks the duality gap
-        asm volatile("bar.sync 1, 64;\n" ::: "memory");
+        if constexpr (W > 1) asm volatile("bar.sync 1, 64;\n" ::: "memory");
+        else __syncwarp();
         if (tid == 0) {
           const double cx = sh.red[0][0], by = sh.red[1][0];
           fail |= !(fabs(cx - by) <= tol * (1.0 + fabs(cx)));
@@ -1136,9 +1143,12 @@ struct RegConfig {
 #define LPB_REG_SE(R, C, W)                                                                         \
   RegConfig{R, C, W, reinterpret_cast<const void *>(&reg_kernel<R, C, W, false>),                   \
             reinterpret_cast<const void *>(&reg_kernel<R, C, W, true>), reg_fixed_bytes<R, C, W>()}
+// One-warp CTAs (W = 1) serve batches of tiny LPs (m, n <= 31): one warp per
+// LP, so that an SM holds many LPs at once and a pivot costs one warp's work.
 const RegConfig kRegConfigs[] = {
     LPB_REG(1, 8, 4), LPB_REG(2, 16, 4), LPB_REG(4, 26, 4), LPB_REG(4, 32, 4),
     LPB_REG_SE(1, 4, 8), LPB_REG_SE(2, 8, 8), LPB_REG_SE(4, 13, 8), LPB_REG_SE(4, 16, 8),
+    LPB_REG_SE(1, 8, 1), LPB_REG_SE(1, 16, 1), LPB_REG_SE(1, 32, 1),
 };
 #undef LPB_REG
 #undef LPB_REG_SE

@@ -53,6 +53,30 @@ def test_type1_m100_sample(solver, prec, rtol, kernel, threads):
             check_unique=prec != "fp32")
 
 
+@pytest.mark.parametrize("m,n", [(1, 1), (5, 5), (7, 7), (12, 15), (16, 16), (31, 7), (9, 31), (31, 31)])
+@pytest.mark.parametrize("prec,rtol", [("fp32_refine", 1e-8), ("fp32", 1e-5)])
+def test_one_warp_templates(solver, m, n, prec, rtol):
+    """Tiny LPs, one warp per LP (the default when every LP has m, n <= 31), at and near the
+    8-, 16- and 32-column limits, against the oracle and against the 8-warp templates."""
+    sb = synth.type1(300, m, n, seed=7 * m + n)
+    got = run(solver, sb, prec)
+    compare(sb, got, obj_rtol=rtol, kkt_tol=1e-8 if prec != "fp32" else 1e-4, check_unique=prec != "fp32")
+    wide = run(solver, sb, prec, reg_warps=8)
+    assert np.array_equal(got["status"], wide["status"])
+    assert np.allclose(got["obj"], wide["obj"], rtol=rtol, atol=0)
+
+
+def test_one_warp_templates_mixed_and_two_phase(solver):
+    """Tiny LPs of mixed sizes with infeasible and unbounded ones (Phase-I LPs leave the
+    register kernel for the tableau kernel)."""
+    sb = synth.type2(400, 24, 20, seed=12, frac_infeasible=0.1, frac_unbounded=0.1)
+    got = run(solver, sb, "fp32_refine")
+    compare(sb, got, obj_rtol=1e-8)
+    sb = synth.mixed_sizes(500, seed=13, lo=1, hi=31)
+    got = run(solver, sb, "fp32_refine")
+    compare(sb, got, obj_rtol=1e-8)
+
+
 @pytest.mark.parametrize("m,n", [(1, 1), (5, 5), (16, 16), (31, 20), (20, 31), (40, 63), (63, 63),
                                  (100, 100), (127, 103), (120, 127)])
 def test_register_kernel_shapes(solver, m, n):
