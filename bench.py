@@ -402,7 +402,8 @@ def secondary_legs(solver, dev):
     sb = synth.type1(1000, 16, 16, seed=0)
     solve_leg("type1_1000x16", LPBatch.from_packed(sb.m, sb.n, sb.A, sb.b, sb.c, device=dev))
     # the m=n sweep at 10,000 LPs (2,000 at 300)
-    for mn, cnt in ((5, 10_000), (28, 10_000), (50, 10_000), (200, 10_000), (300, 2_000)):
+    for mn, cnt in ((5, 10_000), (5, 100_000), (28, 10_000), (28, 100_000), (50, 10_000), (200, 10_000),
+                    (300, 2_000)):
         solve_leg(f"type1_{cnt}x{mn}", _type1_device(cnt, mn, mn, dev, seed=mn), reps=3)
         torch.cuda.empty_cache()
     # the paper's comparison of Step 1 rules (Section 5): the most negative reduced cost
