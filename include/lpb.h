@@ -100,8 +100,8 @@ typedef struct {
 typedef struct {
   int32_t prec;              /* lpb_precision [LPB_FP64] */
   int32_t max_iter;          /* pivot cap per LP [50 (m + n)] */
-  double eps_p;              /* Step 2 eligibility t_ie > eps_p [1e-9 FP64, 1e-6 FP32] */
-  double eps_d;              /* Step 1 eligibility r_j < -eps_d [1e-9 FP64, 1e-6 FP32] */
+  double eps_p;              /* Step 2 eligibility t_ie > eps_p [1e-9 FP64 and the FP64 re-solve, 1e-6 FP32] */
+  double eps_d;              /* Step 1 eligibility r_j < -eps_d [1e-9 FP64 and the FP64 re-solve, 1e-6 FP32] */
   double feas_tol;           /* Phase I / verification tolerance [1e-9] */
   int32_t keep_basis_inverse;/* keep what lpb_solve_backward needs in ws [0] */
   int32_t kernel;            /* lpb_kernel: force a kernel class [LPB_KERNEL_AUTO] */

@@ -86,6 +86,7 @@ struct Plan {
   size_t off_defer = 0, off_resolve = 0, off_basis = 0, off_lists = 0, off_hist = 0, off_cctr = 0,
          off_slots = 0, total = 0;
   double eps_p = 0, eps_d = 0, feas_tol = 0;
+  double eps_p64 = 0, eps_d64 = 0;     // the FP64 re-solve's: FP64 defaults unless given
 };
 
 // Threads per CTA of the tableau kernel: about 1024 threads per SM (512 for
@@ -190,6 +191,8 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   const bool fp32 = o->prec != LPB_FP64;
   pl->eps_p = o->eps_p > 0 ? o->eps_p : (fp32 ? 1e-6 : 1e-9);
   pl->eps_d = o->eps_d > 0 ? o->eps_d : (fp32 ? 1e-6 : 1e-9);
+  pl->eps_p64 = o->eps_p > 0 ? o->eps_p : 1e-9;
+  pl->eps_d64 = o->eps_d > 0 ? o->eps_d : 1e-9;
   pl->feas_tol = o->feas_tol > 0 ? o->feas_tol : 1e-9;
   lpb_err e;
   const int mode = o->prec == LPB_FP64 ? MODE_FP64 : o->prec == LPB_FP32 ? MODE_FP32 : MODE_FP32_REFINE;
@@ -406,9 +409,11 @@ lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_ba
         p.in = WorkList{p.defer_items, p.defer_count};
         p.defer_items = nullptr;   // kcap = max_m: nothing is deferred again
         break;
-      default:
+      default:                 // FP64 re-solve: FP64 tolerances
         p.in = WorkList{p.resolve_items, p.resolve_count};
         p.warm = 1;
+        p.eps_p = pl.eps_p64;
+        p.eps_d = pl.eps_d64;
         break;
     }
     const cudaError_t ce = ps.reg >= 0 ? launch_reg(p, ps.reg, ps.grid, ps.smem, s)
