@@ -1022,7 +1022,17 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
         const double w0 = -double(S.at(m + 1, S.nc));
         const double ftol = sizeof(T) == 4 ? fmax(P.feas_tol * (1.0 + bmax), 1e-5 * (1.0 + w0))
                                            : P.feas_tol * (1.0 + bmax);
-        status = run_phase(S, m + 1, m + 2, 1, iters, max_iter, eps_p, eps_d, P.rule, P.seed, P.lp_base + lp);
+        // FP32 Phase-I reduced costs carry round-off relative to the Phase-I
+        // row, a sum over the negated rows: Step 1's threshold scales with its
+        // largest starting entry, so that round-off does not make columns
+        // eligible.  (The certificate and the FP64 re-solve keep the results
+        // exact.)
+        T eps_d1 = eps_d;
+        if constexpr (sizeof(T) == 4) {
+          const int jm = row_argmax_abs(S, m + 1, T(0), 0);
+          if (jm >= 0) eps_d1 = eps_d * fmaxf(1.f, fabsf(S.at(m + 1, jm)));
+        }
+        status = run_phase(S, m + 1, m + 2, 1, iters, max_iter, eps_p, eps_d1, P.rule, P.seed, P.lp_base + lp);
         if (status == LPB_OPTIMAL) {
           const double w = double(S.at(m + 1, S.nc));
           if (-w > ftol) {
