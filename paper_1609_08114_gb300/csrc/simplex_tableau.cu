@@ -343,13 +343,44 @@ __device__ __forceinline__ void step1_warp(const Tab<T> &S_, int orow, bool blan
   warp_argmin(v, key);
 }
 
+// Phase I: an artificial that has left the basis sits in column e, which no
+// pivot chooses again.  The last column moves into it, the right-hand side
+// moves down one column and its old place is cleared, so that every later
+// pivot sweeps one column less.  Every thread takes part (one row each); the
+// tableau must be stable on entry.  With `remap`, a Step-1 choice of the last
+// column made before the move is redirected to column e.
+template <typename T>
+__device__ __forceinline__ void drop_column(Tab<T> &S, int rows, int e, bool remap) {
+  const int last = S.nc - 1;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    T *r = S.row(i);
+    if (e != last) r[e] = r[last];
+    r[last] = r[S.nc];
+    r[S.nc] = T(0);
+  }
+  if (threadIdx.x == 0) {
+    if (e != last) S.nonb[e] = S.nonb[last];
+    if (remap) {
+      const int k = S.sel[0];
+      if (k != INT_MAX && (k & kIdxMask) == last) S.sel[0] = (k & ~kIdxMask) | e;
+    }
+  }
+  S.nc = last;
+  __syncthreads();
+}
+
 // Steps 1-3 on objective row `orow` until a halt condition (Section 3.1).
 // Phase 1 also ratio-tests rows whose basic variable is artificial; phase 2
-// skips them (they are redundant rows left after Phase I).
+// skips them (they are redundant rows left after Phase I).  Phase 1 drops the
+// columns of artificials that leave the basis; S_.nc returns the new width.
 template <typename T>
-__device__ __forceinline__ int run_phase(const Tab<T> &S_, int orow, int rows, int phase, int &iters, int max_iter,
+__device__ __forceinline__ int run_phase(Tab<T> &S_, int orow, int rows, int phase, int &iters, int max_iter,
                          T eps_p, T eps_d, int rule, unsigned long long seed, long long lp) {
-  const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
+  Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
+  auto done = [&](int status) {
+    S_.nc = S.nc;
+    return status;
+  };
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int r0, r1;
   own_rows(rows, r0, r1);
@@ -375,7 +406,7 @@ __device__ __forceinline__ int run_phase(const Tab<T> &S_, int orow, int rows, i
     const int ekey = S.sel[0];
     if (ekey == INT_MAX) {
       __syncthreads();       // the last pivot row copy is visible to every warp
-      return LPB_OPTIMAL;
+      return done(LPB_OPTIMAL);
     }
     const int e = ekey & kIdxMask;
     // Step 2 on this warp's rows, and the reciprocal of its best pivot.
@@ -436,8 +467,8 @@ __device__ __forceinline__ int run_phase(const Tab<T> &S_, int orow, int rows, i
     int lkey = INT_MAX;
     if (lane < nw) { theta = S.redv[32 + lane]; lkey = S.redk[32 + lane]; }
     warp_argmin(theta, lkey);
-    if (lkey == INT_MAX) return phase == 2 ? LPB_UNBOUNDED : LPB_NUMERIC;
-    if (iters >= max_iter) return LPB_ITER_LIMIT;
+    if (lkey == INT_MAX) return done(phase == 2 ? LPB_UNBOUNDED : LPB_NUMERIC);
+    if (iters >= max_iter) return done(LPB_ITER_LIMIT);
     const int l = lkey & kIdxMask, leave = lkey >> kIdxBits;
     const T rp = S.rcp[l / per];
     if (threadIdx.x == 0) {
@@ -461,6 +492,10 @@ __device__ __forceinline__ int run_phase(const Tab<T> &S_, int orow, int rows, i
     }
     __syncthreads();
     pivot_finish(S, rows, l);
+    if (phase == 1 && leave >= S.nm) {   // the artificial's new column is dead
+      __syncthreads();                   // the pivot row is in place
+      drop_column(S, rows, e, true);
+    }
     if (se) {
       __syncthreads();       // the pivot row is in place
       se_weights(S, orow, phase, eps_d);
@@ -1041,7 +1076,11 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
             for (int i = 0; i < m; ++i) {
               if (S.basic[i] < S.nm) continue;
               const int e = row_argmax_abs(S, i, eps_p, 0);
-              if (e >= 0) { pivot(S, m + 2, i, e); ++iters; }
+              if (e >= 0) {
+                pivot(S, m + 2, i, e);
+                ++iters;
+                drop_column(S, m + 2, e, false);
+              }
               __syncthreads();
             }
           }
