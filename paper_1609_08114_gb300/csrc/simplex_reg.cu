@@ -2,13 +2,17 @@
 // feasible (all b_i >= 0), with the FP64 refinement and verification fused in.
 //
 // Section 3.1 Steps 1-3 on one LP per CTA of W warps (Section 4.1: a block of
-// threads per LP).  Type-1 LPs of the paper's sizes take only ~13 pivots at
-// m = n = 100, so a solve is dominated by moving the LP on chip and by the
-// latency of each pivot, not by the rank-1 arithmetic.  Design:
+// threads per LP; W = 1 gives one warp per tiny LP).  Type-1 LPs of the
+// paper's sizes take only ~13 pivots at m = n = 100, so a solve is dominated
+// by moving the LP on chip and by the latency of each pivot, not by the
+// rank-1 arithmetic.  Design:
 //
-//   * The LP's input A (FP64 or FP32, as given) is copied once into shared
-//     memory with asynchronous copies (one memory round trip) and stays there
-//     for the whole solve; the FP64 refinement reads it back from there.
+//   * The LP's input A, b and c (FP64 or FP32, as given) arrive in shared
+//     memory by bulk copies on one transaction barrier (or by asynchronous
+//     copies when not 16-byte aligned) and A stays there for the whole solve;
+//     the FP64 refinement reads it back from there.  The next LP is claimed
+//     in stages while this one is solved, and its copies are issued as soon
+//     as this LP's certificate has read A, b and c for the last time.
 //   * The compact FP32 tableau lives in registers: lane l of every warp owns
 //     rows l, l+32, ..., l+32(R-1); warp w owns columns w, w+W, ..., w+W(C-1).
 //     The objective row sits at the fixed row 32R-1 (lane 31, register row
@@ -16,25 +20,27 @@
 //     column C-1); rows and columns between the LP's edge and those slots are
 //     zero and stay zero under pivoting, so they need no masks.
 //   * Step 1: each warp judges its own columns (lane c takes column w + W c)
-//     and the W candidates meet in shared memory.
-//   * Step 2: the pivot column lives in one warp (its lanes hold the rows), so
-//     the min-ratio test is a warp reduction with no block barrier.
-//   * Step 3: the lane owning the pivot row scales it by 1/pivot in place; each
-//     warp takes its part of it by shuffles and the pivot column from shared
-//     memory; the update is R x C FMAs per lane.  Two block barriers per pivot.
+//     by the largest-coefficient, random or steepest-edge rule.
+//   * Step 2: each warp runs the min-ratio test on its own candidate column
+//     (its lanes hold the rows: a warp reduction), and after the one block
+//     barrier of the pivot every warp takes the best of the W candidates.
+//   * Step 3: each warp takes the pivot row from its owner lane by shuffles
+//     and the pivot column from the winning warp's shared-memory slot; the
+//     update is R x C FMAs per lane.
 //   * Arg-min reductions use the warp reduction instruction on an
 //     order-preserving integer image of the float (value first, then key).
 //
-// FP64 input is rounded to FP32 in integer arithmetic (d2f_rn): the FP64 unit
-// of this GPU, which also converts double to float, is a small fraction of the
-// FP32 rate.
+// FP64 input is rounded to FP32 in integer arithmetic (d2f_tile, d2f_trunc):
+// the FP64 unit of this GPU, which also converts double to float, is a small
+// fraction of the FP32 rate.
 //
 // After an FP32 optimum the basis inverse is in the registers (the columns of
-// the non-basic slacks).  One step of iterative refinement with FP64 residuals
-// gives x_B and y; an FP64 KKT certificate (x >= 0, A x <= b, y >= 0,
-// A^T y >= c, c^T x = b^T y) decides between writing the result and queueing
-// the LP for the FP64 re-solve.  LPs with some b_i < 0 (Phase I), or larger
-// than the template, or with non-finite data go to the shared-memory kernel.
+// the non-basic slacks).  Iterative refinement with FP64 residuals gives x_B
+// and y; an FP64 KKT certificate (x >= 0, A x <= b, y >= 0, A^T y >= c,
+// c^T x = b^T y) decides between writing the result and, after up to two more
+// refinement rounds, queueing the LP for the FP64 re-solve.  LPs with some
+// b_i < 0 (Phase I), or larger than the template, or with non-finite data go
+// to the shared-memory kernel.
 #include <type_traits>
 
 #include "lpb_internal.cuh"
@@ -403,9 +409,6 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     // ---- admission: sizes that fit the template, b >= 0, finite b and c ----
     const bool fits = fits_lp(m, n);
     const unsigned char *Ag = static_cast<const unsigned char *>(P.B.A) + aoff * es;
-    // Rows of A whose global start and length are whole 16-byte units go by
-    // bulk copy (the copy engine, one instruction per row); others by 4- or
-    // 8-byte asynchronous copies.
     // A is contiguous in global memory: when its start and size are whole
     // 16-byte units it comes in one bulk copy and keeps its row length in
     // shared memory (one copy instruction instead of one per row, at the price
