@@ -76,3 +76,24 @@ def test_struct_layouts_match_header(tmp_path):
         assert int(got[cname]) == ctypes.sizeof(cls), cname
         for f in fields:
             assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+def test_enum_values_match_header(tmp_path):
+    """Every constant of the binding equals the header's enumerator of the same name."""
+    from paper_1609_08114_gb300 import _lib
+    names = ["OPTIMAL", "INFEASIBLE", "UNBOUNDED", "ITER_LIMIT", "NUMERIC", "BAD_SIZE",
+             "OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSUPPORTED", "EDEVICE",
+             "FP64", "FP32_REFINE", "FP32", "DTYPE_F32", "DTYPE_F64",
+             "KERNEL_AUTO", "KERNEL_SMEM", "KERNEL_GMEM", "KERNEL_REG",
+             "PIVOT_LPC", "PIVOT_RPC", "PIVOT_STEEPEST"]
+    prog = tmp_path / "enums.c"
+    body = "".join(f'printf("{n} %d\\n", (int)LPB_{n});' for n in names)
+    prog.write_text('#include <stdio.h>\n#include "lpb.h"\nint main(void){' + body + "return 0;}")
+    exe = tmp_path / "enums"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for n in names:
+        assert int(got[n]) == getattr(_lib, n), n
+    from paper_1609_08114_gb300 import PIVOT_RULES
+    assert PIVOT_RULES == {"lpc": _lib.PIVOT_LPC, "rpc": _lib.PIVOT_RPC, "steepest": _lib.PIVOT_STEEPEST}
