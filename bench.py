@@ -265,7 +265,8 @@ def main():
     # the timed region includes every host<->device copy of the inputs and results.
     from paper_1609_08114_gb300 import SolveResult
     hbatch = LPBatch(*(t.cpu().pin_memory() for t in (batch.m, batch.n, batch.a_off, batch.b_off, batch.c_off,
-                                                      batch.A, batch.b, batch.c)), batch.max_m, batch.max_n)
+                                                      batch.A, batch.b, batch.c)), batch.max_m, batch.max_n,
+                     batch.min_m, batch.min_n)
     hres = SolveResult(torch.empty(batch.count, dtype=torch.int32).pin_memory(), None,
                        torch.empty(batch.count, dtype=torch.float64).pin_memory(),
                        torch.empty(batch.c.numel(), dtype=torch.float64).pin_memory(), None, None)

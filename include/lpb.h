@@ -70,7 +70,10 @@ typedef enum { LPB_DTYPE_F32 = 0, LPB_DTYPE_F64 = 1 } lpb_dtype;
  * elements at b_off[k] of b, its c has n[k] elements at c_off[k] of c.
  * m, n, a_off, b_off, c_off, A, b, c are device pointers.  max_m and max_n are
  * HOST values bounding every m[k] and n[k]; LPs outside them get LPB_BAD_SIZE.
- * dtype (lpb_dtype) applies to A, b and c. */
+ * dtype (lpb_dtype) applies to A, b and c.  min_m and min_n are optional HOST
+ * hints (0 = unknown): min_m = max_m and min_n = max_n tell the planner that
+ * every LP has the same size, which saves the size classification and the
+ * passes of empty size classes (a wrong hint costs speed, not correctness). */
 typedef struct {
   int32_t count;
   int32_t max_m, max_n;
@@ -78,6 +81,7 @@ typedef struct {
   const int32_t *m, *n;
   const int64_t *a_off, *b_off, *c_off;
   const void *A, *b, *c;
+  int32_t min_m, min_n;
 } lpb_batch;
 
 /* Caller-owned device outputs, FP64 whatever the input dtype.  status, iters

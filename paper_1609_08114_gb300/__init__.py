@@ -43,11 +43,13 @@ class LPBatch:
     """A packed batch on the device: LP k's ``A`` (m_k x n_k, row-major) at ``a_off[k]``,
     ``b`` at ``b_off[k]``, ``c`` at ``c_off[k]``."""
 
-    def __init__(self, m, n, a_off, b_off, c_off, A, b, c, max_m: int, max_n: int):
+    def __init__(self, m, n, a_off, b_off, c_off, A, b, c, max_m: int, max_n: int, min_m: int = 0,
+                 min_n: int = 0):
         self.m, self.n = m, n
         self.a_off, self.b_off, self.c_off = a_off, b_off, c_off
         self.A, self.b, self.c = A, b, c
         self.max_m, self.max_n = int(max_m), int(max_n)
+        self.min_m, self.min_n = int(min_m), int(min_n)     # size hints, 0 = unknown
 
     @property
     def count(self) -> int:
@@ -72,12 +74,13 @@ class LPBatch:
         return cls(to(m, torch.int32), to(n, torch.int32), to(offs[0], torch.int64), to(offs[1], torch.int64),
                    to(offs[2], torch.int64), to(A, dtype), to(b, dtype), to(c, dtype),
                    max_m if max_m is not None else (int(m.max()) if len(m) else 1),
-                   max_n if max_n is not None else (int(n.max()) if len(n) else 1))
+                   max_n if max_n is not None else (int(n.max()) if len(n) else 1),
+                   int(m.min()) if len(m) else 0, int(n.min()) if len(n) else 0)
 
     def pin_memory(self) -> "LPBatch":
         """A copy of a host batch in page-locked memory (for ``Solver.solve_host``)."""
         t = [x.pin_memory() for x in (self.m, self.n, self.a_off, self.b_off, self.c_off, self.A, self.b, self.c)]
-        return LPBatch(*t, self.max_m, self.max_n)
+        return LPBatch(*t, self.max_m, self.max_n, self.min_m, self.min_n)
 
     @classmethod
     def from_dense(cls, A: torch.Tensor, b: torch.Tensor, c: torch.Tensor):
@@ -88,13 +91,14 @@ class LPBatch:
         return cls(torch.full((count,), m, dtype=torch.int32, device=dev),
                    torch.full((count,), n, dtype=torch.int32, device=dev),
                    ar * (m * n), ar * m, ar * n, A.contiguous().view(-1), b.contiguous().view(-1),
-                   c.contiguous().view(-1), m, n)
+                   c.contiguous().view(-1), m, n, m, n)
 
     def cstruct(self) -> _lib.Batch:
         dt = {torch.float32: _lib.DTYPE_F32, torch.float64: _lib.DTYPE_F64}[self.A.dtype]
         assert self.b.dtype == self.A.dtype and self.c.dtype == self.A.dtype
         return _lib.Batch(self.count, self.max_m, self.max_n, dt, _ptr(self.m), _ptr(self.n), _ptr(self.a_off),
-                          _ptr(self.b_off), _ptr(self.c_off), _ptr(self.A), _ptr(self.b), _ptr(self.c))
+                          _ptr(self.b_off), _ptr(self.c_off), _ptr(self.A), _ptr(self.b), _ptr(self.c),
+                          self.min_m, self.min_n)
 
 
 @dataclass

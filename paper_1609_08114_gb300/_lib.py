@@ -31,7 +31,7 @@ P = ctypes.c_void_p
 class Batch(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("max_m", ctypes.c_int32), ("max_n", ctypes.c_int32),
                 ("dtype", ctypes.c_int32), ("m", P), ("n", P), ("a_off", P), ("b_off", P),
-                ("c_off", P), ("A", P), ("b", P), ("c", P)]
+                ("c_off", P), ("A", P), ("b", P), ("c", P), ("min_m", ctypes.c_int32), ("min_n", ctypes.c_int32)]
 
 
 class Result(ctypes.Structure):

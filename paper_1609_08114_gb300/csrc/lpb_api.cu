@@ -201,10 +201,12 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   const int want_w = o->reg_warps > 0 ? o->reg_warps
                    : (o->kernel == LPB_KERNEL_REG && o->threads > 0) ? o->threads / 32
                    : (b->max_m <= 31 && b->max_n <= 31) ? 1 : 8;
+  // Every LP of the same size (the caller's hint): one pass, no size classes.
+  const bool uniform = b->min_m > 0 && b->min_m == b->max_m && b->min_n == b->max_n;
   lpb_options og = *o;          // options of the shared-memory / L2-slot kernel passes
   if (og.kernel == LPB_KERNEL_REG) { og.kernel = LPB_KERNEL_AUTO; og.threads = 0; }
   int np = 0;
-  if (fp32 && o->kernel == LPB_KERNEL_AUTO) {
+  if (fp32 && o->kernel == LPB_KERNEL_AUTO && !uniform) {
     // Size classes: the register-tableau templates with `want_w` warps in
     // increasing size, then the shared-memory / L2-slot kernel for the rest.
     Pass regp[kMaxClasses];
@@ -256,7 +258,8 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   }
   if (np == 0) {                   // one first pass over every LP
     Pass &p = pl->pass[0];
-    const int reg = (fp32 && o->kernel == LPB_KERNEL_REG) ? reg_pick(b->max_m, b->max_n, want_w, se) : -1;
+    const int reg = fp32 && (o->kernel == LPB_KERNEL_REG || (o->kernel == LPB_KERNEL_AUTO && uniform))
+                        ? reg_pick(b->max_m, b->max_n, want_w, se) : -1;
     if (o->kernel == LPB_KERNEL_REG && reg < 0) return LPB_EUNSUPPORTED;
     if (reg >= 0) {
       if ((e = reg_pass(d, b, reg, b->max_m, b->max_n, mode, o->pivot_rule, &p)) != LPB_OK) return e;
@@ -652,6 +655,7 @@ lpb_err make_bounded_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_opt
   if (b->dtype != LPB_DTYPE_F64) return LPB_EUNSUPPORTED;   // the reduced LP reads the caller's c as FP64
   if (b->max_m + b->max_n > kMaxDim) return LPB_EUNSUPPORTED;
   lpb_batch rb = *b;
+  rb.min_m = rb.min_n = 0;      // the reduced LPs have m + n rows
   rb.max_m = b->max_m + b->max_n;
   rb.dtype = LPB_DTYPE_F64;
   const lpb_err e = solve_workspace_bytes(d, &rb, o, false, &bp->solve_ws);

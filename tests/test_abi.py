@@ -56,7 +56,8 @@ def test_struct_layouts_match_header(tmp_path):
     from paper_1609_08114_gb300 import _lib
     prog = tmp_path / "layout.c"
     checks = {
-        "lpb_batch": (_lib.Batch, ["count", "max_m", "max_n", "dtype", "m", "n", "a_off", "b_off", "c_off", "A", "b", "c"]),
+        "lpb_batch": (_lib.Batch, ["count", "max_m", "max_n", "dtype", "m", "n", "a_off", "b_off", "c_off", "A", "b", "c",
+                                   "min_m", "min_n"]),
         "lpb_result": (_lib.Result, ["status", "iters", "obj", "x", "y", "basis"]),
         "lpb_options": (_lib.Options, ["prec", "max_iter", "eps_p", "eps_d", "feas_tol", "keep_basis_inverse",
                                        "kernel", "threads", "reg_warps", "pivot_rule", "seed"]),
