@@ -98,3 +98,19 @@ def test_enum_values_match_header(tmp_path):
         assert int(got[n]) == getattr(_lib, n), n
     from paper_1609_08114_gb300 import PIVOT_RULES
     assert PIVOT_RULES == {"lpc": _lib.PIVOT_LPC, "rpc": _lib.PIVOT_RPC, "steepest": _lib.PIVOT_STEEPEST}
+
+
+def test_batch_size_hints():
+    """LPBatch carries the host size hints the planner uses (min = max: one size class)."""
+    import numpy as np
+    import torch
+    from paper_1609_08114_gb300 import LPBatch
+    m, n = np.array([3, 5, 4]), np.array([2, 2, 6])
+    A = np.ones(int((m * n).sum())); b = np.ones(int(m.sum())); c = np.ones(int(n.sum()))
+    bt = LPBatch.from_packed(m, n, A, b, c, device="cpu")
+    assert (bt.max_m, bt.max_n, bt.min_m, bt.min_n) == (5, 6, 3, 2)
+    cs = bt.cstruct()
+    assert (cs.max_m, cs.max_n, cs.min_m, cs.min_n) == (5, 6, 3, 2)
+    d = LPBatch.from_dense(torch.ones(4, 7, 3, dtype=torch.float64), torch.ones(4, 7, dtype=torch.float64),
+                           torch.ones(4, 3, dtype=torch.float64))
+    assert (d.max_m, d.max_n, d.min_m, d.min_n) == (7, 3, 7, 3)
