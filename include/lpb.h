@@ -154,12 +154,15 @@ lpb_err lpb_create(lpb_handle **handle, int device);
 lpb_err lpb_destroy(lpb_handle *handle);
 
 /* Workspace bytes lpb_solve / lpb_solve_backward need for this batch shape
- * and these options (depends only on count, max_m, max_n, dtype, options). */
+ * and these options (depends only on count, max_m, max_n, min_m, min_n,
+ * dtype and the options; a solve whose batch declares other sizes than the
+ * query may need more and then returns LPB_ENOMEM before any launch). */
 lpb_err lpb_workspace_size(lpb_handle *handle, const lpb_batch *batch, const lpb_options *opt,
                            size_t *bytes);
 
-/* Solve every LP of the batch (Section 3.1 Steps 1-3 with Dantzig's rule,
- * Phase I of Section 3 when some b_i < 0).  Asynchronous on `stream`. */
+/* Solve every LP of the batch (Section 3.1 Steps 1-3 with the entering rule
+ * opt->pivot_rule, Dantzig's by default; Phase I of Section 3 when some
+ * b_i < 0).  Asynchronous on `stream`. */
 lpb_err lpb_solve(lpb_handle *handle, const lpb_batch *batch, const lpb_options *opt,
                   const lpb_result *result, void *ws, size_t ws_bytes, void *stream);
 
@@ -188,7 +191,7 @@ lpb_err lpb_hyperbox(lpb_handle *handle, int64_t count, int32_t n, int32_t dtype
 
 /* Autotuner.  Picks, for batches shaped like `batch` (same max_m, max_n,
  * dtype and precision), the fastest schedule among: warps per LP of the
- * register kernel (4 or 8), threads per CTA of the tableau kernel (automatic,
+ * register kernel (1, 4 or 8), threads per CTA of the tableau kernel (automatic,
  * 256, 512 or 1024) and its placement (shared memory when it fits, or
  * L2-resident slots).
  * If `table_path` (may be NULL) holds an entry for this shape, that entry is
