@@ -304,6 +304,16 @@ lpb_err lpb_solve_bounded(lpb_handle *handle, const lpb_batch *batch, const void
 lpb_err lpb_solve_noalloc(const lpb_batch *batch, const lpb_options *opt, const lpb_result *result,
                           void *stream);
 
+/* The device error word of lpb_solve_noalloc, which lives in the same fixed
+ * array (the paper has no counterpart; see lpb_solve_noalloc).  Synchronises
+ * `stream`, copies the word of the current device into *word (when non-NULL)
+ * and clears it.  Returns LPB_OK (word == 0), LPB_EDEVICE (a kernel of an
+ * earlier lpb_solve_noalloc recorded a fault: the bits are those that
+ * lpb_sync_error reports) or LPB_ECUDA.  Read it before the next
+ * lpb_solve_noalloc on the device, which starts by clearing the word.
+ * Allocates nothing. */
+lpb_err lpb_noalloc_sync_error(void *stream, uint32_t *word);
+
 /* Kernel timing.  lpb_profile_start(h, calls) makes the next `calls` (<= 256)
  * lpb_solve calls record a CUDA event pair on their stream around each of
  * their kernel passes (pass 0: every LP; pass 1: LPs needing more artificial

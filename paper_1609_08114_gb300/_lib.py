@@ -81,6 +81,7 @@ SIGNATURES = {
     "lpb_get_stats": (ctypes.c_int, [P, P, ctypes.POINTER(Stats)]),
     "lpb_solve_noalloc": (ctypes.c_int, [ctypes.POINTER(Batch), ctypes.POINTER(Options), ctypes.POINTER(Result),
                                          P]),
+    "lpb_noalloc_sync_error": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_uint32)]),
     "lpb_profile_start": (ctypes.c_int, [P, ctypes.c_int32]),
     "lpb_profile_read": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32,
                                         ctypes.POINTER(ctypes.c_int32)]),

@@ -204,18 +204,21 @@ __global__ void hyperbox_tma_kernel(HyperboxParams P, int lps, uint32_t *err) {
     const int s = int(k % kStages);
     const unsigned phase = unsigned((k / kStages) & 1);
     const int64_t chunk = blockIdx.x + k * gridDim.x;
-    unsigned tries = 0;
-    while (!mbar_try_wait(&bars[s], phase)) {
-      if (++tries >= kWaitLimit) { failed = true; break; }
-    }
+    failed = !mbar_wait_for(&bars[s], phase, kCopyWaitNs);
     if (__syncthreads_or(failed)) {
       if (tid == 0) {
         atomicOr(err, ERR_WAIT_TIMEOUT);
-        // Let the copies this CTA issued land before it exits (bounded again):
-        // stage s2 still expects the completion of chunk k2 = k, k+1, ... < mine.
+        // Let the copies this CTA issued land before it exits (bounded again, by
+        // kDrainWaitNs in all): stage s2 still expects the completion of chunk
+        // k2 = k, k+1, ... < mine.  If they do not, the CTA leaves with copies
+        // outstanding and says so in the error word.
+        const unsigned long long t0 = global_ns();
         for (int64_t k2 = k; k2 < k + kStages && k2 < mine; ++k2) {
-          unsigned t2 = 0;
-          while (!mbar_try_wait(&bars[k2 % kStages], unsigned((k2 / kStages) & 1)) && ++t2 < kWaitLimit) {
+          const unsigned long long used = global_ns() - t0;
+          if (used > kDrainWaitNs ||
+              !mbar_wait_for(&bars[k2 % kStages], unsigned((k2 / kStages) & 1), kDrainWaitNs - used)) {
+            atomicOr(err, ERR_COPY_IN_FLIGHT);
+            break;
           }
         }
       }

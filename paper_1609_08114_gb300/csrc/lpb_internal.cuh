@@ -24,6 +24,10 @@ enum : uint32_t {
   ERR_SLOT_OVERFLOW = 2u,   // an LP did not fit the tableau slot of its launch
   ERR_BAD_LAUNCH = 4u,      // a kernel was launched with an inconsistent configuration
   ERR_WAIT_TIMEOUT = 8u,    // a bounded wait on an asynchronous copy gave up
+  ERR_COPY_IN_FLIGHT = 16u, // a CTA left while copies into its shared memory were still
+                            // outstanding (only after ERR_WAIT_TIMEOUT and a second deadline):
+                            // the shared memory of CTAs that run on that SM after it may be
+                            // overwritten, so no result of that launch can be trusted
 };
 
 enum Mode : int { MODE_FP64 = 0, MODE_FP32_REFINE = 1, MODE_FP32 = 2 };
@@ -183,10 +187,16 @@ __device__ __forceinline__ T warp_sum(T v) {
 // ---- bulk asynchronous copies (TMA engine) and transaction mbarriers ------
 //
 // A bulk copy needs 16-byte aligned source and destination and a size that is
-// a multiple of 16 bytes.  Waits on an mbarrier are bounded by kWaitLimit
-// try_wait rounds; callers turn a timeout into ERR_WAIT_TIMEOUT.
+// a multiple of 16 bytes.  Waits on an mbarrier are bounded in time, by the
+// GPU's global nanosecond timer: a copy of a few hundred KB lands in
+// microseconds, so kCopyWaitNs (20 ms, room for the SM being time-sliced with
+// other contexts) marks a copy as failed (callers record ERR_WAIT_TIMEOUT and
+// hand the work elsewhere); before the CTA leaves, it waits up to kDrainWaitNs
+// (1 s) more for the copies it issued, and records ERR_COPY_IN_FLIGHT if even
+// that runs out.
 
-constexpr unsigned kWaitLimit = 1u << 26;
+constexpr unsigned long long kCopyWaitNs = 20ull * 1000 * 1000;
+constexpr unsigned long long kDrainWaitNs = 1000ull * 1000 * 1000;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -205,11 +215,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase) {
                : "=r"(ok) : "r"(smem_u32(bar)), "r"(phase) : "memory");
   return ok != 0;
 }
-// Wait for `phase` of `bar` to complete; false after kWaitLimit rounds.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned phase) {
-  for (unsigned tries = 0; tries < kWaitLimit; ++tries)
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for `phase` of `bar` to complete; false once `ns` nanoseconds have
+// passed without it.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, unsigned phase, unsigned long long ns) {
+  const unsigned long long t0 = global_ns();
+  for (;;) {
     if (mbar_try_wait(bar, phase)) return true;
-  return false;
+    if (global_ns() - t0 > ns) return false;
+  }
 }
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"

@@ -90,3 +90,20 @@ extern "C" lpb_err lpb_solve_noalloc(const lpb_batch *b, const lpb_options *o, c
   return lpb::run_solve(s->info, ctr, err, b, o, r, s->base + kHeaderBytes, kNoAllocBytes - kHeaderBytes, st,
                         nullptr, nullptr);
 }
+
+// The device error word of lpb_solve_noalloc lives in the same fixed array, so
+// its callers read it here rather than through a handle: wait for `stream`,
+// copy the word into the caller's host variable, clear it.  No allocation.
+extern "C" lpb_err lpb_noalloc_sync_error(void *stream, uint32_t *word) {
+  DeviceScratch *s = nullptr;
+  const lpb_err e = scratch_for_current_device(&s);
+  if (e != LPB_OK) return e;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t *err = reinterpret_cast<uint32_t *>(s->base + lpb::kCounters * sizeof(int32_t));
+  uint32_t v = 0;
+  if (cudaMemcpyAsync(&v, err, sizeof(v), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemsetAsync(err, 0, sizeof(uint32_t), st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+    return LPB_ECUDA;
+  if (word) *word = v;
+  return v ? LPB_EDEVICE : LPB_OK;
+}

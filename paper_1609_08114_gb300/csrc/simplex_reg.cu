@@ -479,20 +479,22 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
     cp_async_wait_all();
     int timed_out = 0;
     if (dense || bulk || bulk_bc || bulk_c) {
-      timed_out = !mbar_wait_bounded(&sh.abar, aphase);
+      timed_out = !mbar_wait_for(&sh.abar, aphase, kCopyWaitNs);
       aphase ^= 1u;
     }
     const int any_timeout = __syncthreads_or(timed_out);
     if (tid == 0) sh.pre = 0;
     if (any_timeout) {
       // The copy engine did not deliver the data in time: hand this LP and the one
-      // claimed after it to the generic kernel, give the copies one more
-      // bounded wait, and stop this CTA.
+      // claimed after it to the generic kernel, wait up to kDrainWaitNs more for
+      // the copies to land, and stop this CTA.  Only if that wait runs out too
+      // does the CTA leave with copies into its shared memory outstanding; it
+      // then records ERR_COPY_IN_FLIGHT, which voids the launch's results.
       if (tid == 0) {
         atomicOr(P.err, ERR_WAIT_TIMEOUT);
         P.R.status[lp] = STATUS_PENDING;
         list_push(P.defer_items, P.defer_count, P.list_cap, lp, P.err);
-        mbar_wait_bounded(&sh.abar, aphase ^ 1u);
+        if (!mbar_wait_for(&sh.abar, aphase ^ 1u, kDrainWaitNs)) atomicOr(P.err, ERR_COPY_IN_FLIGHT);
       }
       if (tid == claimer && next < nitems) {
         const int lp2 = P.in.items ? P.in.items[next] : next;

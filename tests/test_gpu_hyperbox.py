@@ -68,9 +68,10 @@ def test_full_size_sampled(solver):
 
 
 def test_fp64_products_round_like_ieee(solver):
-    """The FP64 kernel forms each rounded product in integer arithmetic; crafted pairs hit
-    exact ties (round to even, both ways), carries into the exponent, the edges of the normal
-    range, subnormals, zeros and signed zeros.  The oracle's float64 loop is IEEE."""
+    """The FP64 kernel forms each product with a separately rounded multiply (no fused
+    multiply-add into the sum); crafted pairs hit exact ties (round to even, both ways),
+    carries into the exponent, the edges of the normal range, subnormals, zeros and signed
+    zeros.  The oracle's float64 loop is IEEE."""
     eps = 2.0 ** -52
     pairs = [(1 + eps, 1.5), (1 + 3 * eps, 1.5), (1 + eps, 1 + eps), (2 - eps, 1 + eps), (2 - eps, 2 - eps),
              (1.5, 1 + 2 * eps), (3.0, 1 / 3), (2.0 ** 1000, 2.0 ** 23.5), (2.0 ** -1000, 2.0 ** -22),

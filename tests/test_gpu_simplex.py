@@ -1,7 +1,8 @@
 """GPU parity of the batched simplex (liblpb.so through the C ABI) against the FP64 oracle.
 
 Statuses must match exactly; objectives within 1e-9 relative in FP64 and 1e-8 after
-FP32 + FP64 refinement; x* and y to 1e-7 where the oracle certifies the optimum unique;
+FP32 + FP64 refinement; x* and y to the same relative tolerances (norm-wise) where the oracle
+certifies the optimum unique;
 and the GPU's own (x, y) must satisfy KKT in FP64 on every optimal LP.
 """
 import json

@@ -6,7 +6,8 @@ library instead of a caller workspace.
 Called through the C ABI, twice in a row (the second call reuses the array the first one
 left behind), it must give the same results as lpb_solve with a caller workspace, within
 the tolerances the other parity tests use; a batch whose scratch exceeds the array must be
-refused before anything runs.  This file is collected last so that a failure here leaves
+refused before anything runs; and the device error word that these calls keep in the same
+array reads 0 after a clean call (lpb_noalloc_sync_error).  This file is collected last so that a failure here leaves
 every other test already run."""
 import ctypes
 
@@ -51,6 +52,10 @@ def test_noalloc_matches_workspace_solve_twice(prec, rtol):
         assert rel.max() <= rtol, call
         assert np.all(np.abs(got["x"] - want["x"]) <= 1e-7 * (1 + np.abs(want["x"]))), call
         assert np.all(np.abs(got["y"] - want["y"]) <= 1e-7 * (1 + np.abs(want["y"]))), call
+        word = ctypes.c_uint32(0xFFFFFFFF)
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        assert solver.lib.lpb_noalloc_sync_error(stream, ctypes.byref(word)) == _lib.OK, call
+        assert word.value == 0, call                    # a clean call leaves no fault bit
 
 
 def test_noalloc_refuses_batches_beyond_its_scratch():
