@@ -332,6 +332,11 @@ int reg_count();
 void reg_limits(int cfg, int *max_m, int *max_n, int *warps);
 cudaError_t reg_occupancy(int cfg, int max_m, int max_n, int dtype, int rule, int *ctas, int *threads, size_t *smem);
 cudaError_t launch_reg(const TableauParams &p, int cfg, int grid, size_t smem, cudaStream_t s);
+// Several tiny LPs per warp (simplex_pack.cu): lanes per LP for LPs up to
+// max_m x max_n (8 or 16; 0 when they do not fit), occupancy and launch.
+int pack_lanes(int max_m, int max_n);
+cudaError_t pack_occupancy(int lanes, int *ctas, int *threads);
+cudaError_t launch_pack(const TableauParams &p, int lanes, int grid, cudaStream_t s);
 size_t hyperbox_smem_bytes(int n, int elem_bytes, bool shared_box);
 cudaError_t launch_hyperbox(const HyperboxParams &p, uint32_t *err, cudaStream_t s);
 // Backward kernel (backward.cu).

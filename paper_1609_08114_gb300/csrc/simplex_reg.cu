@@ -659,7 +659,9 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
         }
       }
       __syncwarp();
-      float cv = __int_as_float(0x7f800000);
+      // No candidate: the largest value of the order-preserving image, above
+      // every random-rule key (whose bit patterns may exceed that of +inf).
+      float cv = __int_as_float(0x7fffffff);
       int ck = kBad;
       float gam = 1.f;
       if constexpr (SE) {
@@ -702,7 +704,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       if (lane == 0) sh.choice[par][wid] = WarpChoice{cv, ck, tv, tk};
       __syncthreads();
       // The pivot: the best (value, key) over the warps' choices.
-      float ev = __int_as_float(0x7f800000);
+      float ev = __int_as_float(0x7fffffff);
       int ek = kBad;
       if (lane < W) {
         ev = sh.choice[par][lane].v;

@@ -57,14 +57,49 @@ def test_type1_m100_sample(solver, prec, rtol, kernel, threads):
 @pytest.mark.parametrize("m,n", [(1, 1), (5, 5), (7, 7), (12, 15), (16, 16), (31, 7), (9, 31), (31, 31)])
 @pytest.mark.parametrize("prec,rtol", [("fp32_refine", 1e-8), ("fp32", 1e-5)])
 def test_one_warp_templates(solver, m, n, prec, rtol):
-    """Tiny LPs, one warp per LP (the default when every LP has m, n <= 31), at and near the
-    8-, 16- and 32-column limits, against the oracle and against the 8-warp templates."""
+    """Tiny LPs at and near the 8-, 16- and 32-column limits: the default plan (several LPs
+    per warp up to m, n <= 15, one warp per LP up to 31) and the one-warp templates, against
+    the oracle and against the 8-warp templates."""
     sb = synth.type1(300, m, n, seed=7 * m + n)
-    got = run(solver, sb, prec)
-    compare(sb, got, obj_rtol=rtol, kkt_tol=1e-8 if prec != "fp32" else 1e-4, check_unique=prec != "fp32")
     wide = run(solver, sb, prec, reg_warps=8)
-    assert np.array_equal(got["status"], wide["status"])
-    assert np.allclose(got["obj"], wide["obj"], rtol=rtol, atol=0)
+    for kw in ({}, {"reg_warps": 1}):
+        got = run(solver, sb, prec, **kw)
+        compare(sb, got, obj_rtol=rtol, kkt_tol=1e-8 if prec != "fp32" else 1e-4, check_unique=prec != "fp32")
+        assert np.array_equal(got["status"], wide["status"])
+        assert np.allclose(got["obj"], wide["obj"], rtol=rtol, atol=0)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (2, 7), (7, 2), (5, 5), (7, 7), (8, 8), (7, 8), (8, 3), (12, 15), (15, 15),
+                                 (15, 9)])
+@pytest.mark.parametrize("prec,rtol", [("fp32_refine", 1e-8), ("fp32", 1e-5)])
+def test_several_lps_per_warp(solver, m, n, prec, rtol):
+    """Several tiny LPs per warp (four of m, n <= 7 or two of m, n <= 15 in one warp), at and
+    near both segment limits and with a ragged last group (1001 LPs), against the oracle."""
+    from paper_1609_08114_gb300 import KERNEL_PACK
+    sb = synth.type1(1001, m, n, seed=31 * m + n)
+    got = run(solver, sb, prec, kernel=KERNEL_PACK)
+    compare(sb, got, obj_rtol=rtol, kkt_tol=1e-8 if prec != "fp32" else 1e-4, check_unique=prec != "fp32")
+    assert solver.stats()["deferred"] == 0
+    auto = run(solver, sb, prec)                   # the default plan takes the same kernel
+    assert np.array_equal(auto["status"], got["status"]) and np.array_equal(auto["obj"], got["obj"])
+
+
+def test_several_lps_per_warp_all_statuses(solver):
+    """Mixed tiny LPs with Phase I (deferred to the tableau kernel), infeasible and unbounded
+    LPs (confirmed by the FP64 re-solve), integer data with ties and degenerate vertices,
+    and the random pivot rule."""
+    from paper_1609_08114_gb300 import KERNEL_PACK
+    t2 = synth.type2(200, 12, 10, seed=14, frac_infeasible=0.15, frac_unbounded=0.15)
+    lps = [t2.lp(k) for k in range(t2.count)] + _tiny_integer_lps(9, 400)
+    lps += [synth.mixed_sizes(300, seed=15, lo=1, hi=15).lp(k) for k in range(300)]
+    sb = synth.pack(lps)
+    ref = oracle.solve_batch(sb)
+    for kw in ({"kernel": KERNEL_PACK}, {}):
+        got = run(solver, sb, "fp32_refine", **kw)
+        compare(sb, got, ref=ref, obj_rtol=1e-8, check_unique=False)
+    assert set(np.unique(ref["status"])) == {0, 1, 2}
+    got = run(solver, sb, "fp32_refine", kernel=KERNEL_PACK, pivot_rule="rpc", seed=5)
+    compare(sb, got, ref=ref, obj_rtol=1e-8, check_unique=False)
 
 
 def test_one_warp_templates_mixed_and_two_phase(solver):
