@@ -6,12 +6,15 @@ refinement and KKT certificate, FP64 re-solve of failures, outputs.  Prints one 
 (rank 0).  ``--impl reference`` times the CPU oracle on samples of the same workload.
 
 Secondary legs (skip with ``--no-legs``) time the other workloads once each with CUDA
-events: 1,000 x m=n=16; the m=n sweep; the two Step 1 rules (most negative reduced cost
-vs a random eligible column) on 50,000 x m=n=100; one m=n=100 polytope in 50,000
+events: 1,000 x m=n=16; the m=n sweep (5, 7, 12, 15 and 28 at 100,000 LPs: several tiny
+LPs per warp up to 15); the two Step 1 rules (most negative reduced cost vs a random
+eligible column) and steepest edge on 50,000 x m=n=100; one m=n=100 polytope in 50,000
 directions (shared constraints); 10,000 x m=n=100 with bounds l <= x <= u; 10,000 x m=n=200
-two-phase; hyperbox
-support functions (4,000,000 x 5 FP32, 6,000,000 x 28 FP64); 20,000 mixed sizes forward
-and forward+backward.
+two-phase (largest coefficient and steepest edge); hyperbox support functions (4,000,000 x 5
+FP32, 6,000,000 x 28 FP64); 20,000 mixed sizes forward and forward+backward.
+
+``--profile-case`` runs one small workload twice (no bench line) for ncu captures of single
+launches; the commands in ``profiles/`` use it.
 
 Launch: ``python bench.py --gpus 1 --steps K --warmup W``; for N > 1 under
 ``torch.distributed.run`` (one rank per GPU; each rank solves its own 50,000 LPs, weak
@@ -42,7 +45,7 @@ FP32_FMA_PIPES_PER_SM = 128
 # register-tableau kernel, from an ncu capture of a 5,000-LP launch scaled by 10 (DRAM bytes
 # grow with the LPs processed), keyed by the first 16 hex digits of the sha256 of the kernel
 # source it was taken on; a source without an entry reports traffic null.
-PROFILED_DRAM_BYTES = {}
+PROFILED_DRAM_BYTES = {"2a73876d4e443db2": 4189.5e6}
 
 
 def parse():
@@ -486,8 +489,8 @@ def secondary_legs(solver, dev):
     sb = synth.type1(1000, 16, 16, seed=0)
     solve_leg("type1_1000x16", LPBatch.from_packed(sb.m, sb.n, sb.A, sb.b, sb.c, device=dev))
     # the m=n sweep at 10,000 LPs (2,000 at 300)
-    for mn, cnt in ((5, 10_000), (5, 100_000), (28, 10_000), (28, 100_000), (50, 10_000), (200, 10_000),
-                    (300, 2_000)):
+    for mn, cnt in ((5, 10_000), (5, 100_000), (7, 100_000), (12, 100_000), (15, 100_000), (28, 10_000),
+                    (28, 100_000), (50, 10_000), (200, 10_000), (300, 2_000)):
         solve_leg(f"type1_{cnt}x{mn}", _type1_device(cnt, mn, mn, dev, seed=mn), reps=3)
         torch.cuda.empty_cache()
     # the paper's comparison of Step 1 rules (Section 5): the most negative reduced cost
@@ -538,9 +541,13 @@ def secondary_legs(solver, dev):
     out["bounded_10000x100"] = leg
     del bt, lo, hi
     torch.cuda.empty_cache()
-    # 10,000 x m=n=200 two-phase
+    # 10,000 x m=n=200 two-phase, largest-coefficient rule and steepest edge (fewer pivots,
+    # O(m n) weights per pivot)
     sb = synth.type2(10_000, 200, 200, seed=2)
-    solve_leg("type2_10000x200", LPBatch.from_packed(sb.m, sb.n, sb.A, sb.b, sb.c, device=dev), reps=3)
+    bt2 = LPBatch.from_packed(sb.m, sb.n, sb.A, sb.b, sb.c, device=dev)
+    solve_leg("type2_10000x200", bt2, reps=3)
+    solve_leg("type2_10000x200_steepest", bt2, reps=2, pivot_rule="steepest")
+    del bt2
     del sb
     torch.cuda.empty_cache()
     # 20,000 mixed sizes, forward and forward + backward (autograd)

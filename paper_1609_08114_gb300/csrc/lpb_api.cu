@@ -593,6 +593,8 @@ lpb_err make_shared_plan(const DeviceInfo &d, int m, int n, int dtype, int64_t c
   pb.count = int32_t(count);
   pb.max_m = m;
   pb.max_n = n;
+  pb.min_m = m;            // every LP of the batch has the one size m x n
+  pb.min_n = n;
   pb.dtype = dtype;
   const lpb_err e = solve_workspace_bytes(d, &pb, o, false, &sp->solve_ws);
   if (e != LPB_OK) return e;
@@ -991,6 +993,8 @@ lpb_err lpb_solve_shared(lpb_handle *h, int32_t m, int32_t n, int32_t dtype, con
   bt.count = cnt;
   bt.max_m = m;
   bt.max_n = n;
+  bt.min_m = m;
+  bt.min_n = n;
   bt.dtype = dtype;
   bt.m = dm;
   bt.n = dn;

@@ -81,10 +81,40 @@ __device__ __forceinline__ float d2f_rn(double d) {
   return __double2float_rn(d);
 }
 
+// Float -> double, exact, in integer operations for normal floats and zeros
+// (the hardware conversion runs on the slow FP64 unit); subnormal, infinite
+// and NaN inputs take the hardware conversion.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e != 0u && e != 0xffu) {
+    const unsigned hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u >> 3) & 0xfffffu);
+    const unsigned lo = u << 29;
+    return __hiloint2double(int(hi), int(lo));
+  }
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double(int(u & 0x80000000u), 0);
+  return double(f);
+}
+
+// a >= b for finite doubles, compared as integers (sign-magnitude order) so
+// that no FP64 instruction is spent; false when a is not finite.
+__device__ __forceinline__ unsigned long long d2ord(double d) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(d));
+  return (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double neg_bits(double d) {   // -d by the sign bit
+  return __longlong_as_double(__double_as_longlong(d) ^ static_cast<long long>(0x8000000000000000ull));
+}
+__device__ __forceinline__ double abs_bits(double d) {   // |d| by the sign bit
+  return __longlong_as_double(__double_as_longlong(d) & 0x7fffffffffffffffll);
+}
+
 // Finite test on the exponent bits (no FP64 instruction).
 __device__ __forceinline__ bool finite_bits(double d) {
   return (unsigned(static_cast<unsigned long long>(__double_as_longlong(d)) >> 32) & 0x7ff00000u) != 0x7ff00000u;
 }
+
+__device__ __forceinline__ bool dge(double a, double b) { return finite_bits(a) && d2ord(a) >= d2ord(b); }
 
 // Input element `i` as the tableau's type T.
 template <typename T>

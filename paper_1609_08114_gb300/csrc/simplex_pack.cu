@@ -35,6 +35,8 @@ struct PackWarp {
   static constexpr int G = 32 / S;
   alignas(16) float objv[G][S];        // the objective row, published for Step 1
   int nvs[G][S];                       // variable of each non-basic column
+  int sbj[G][S];                       // the basic structural variables (their column of A)
+  int nsk[G][S];                       // the rows whose slack is non-basic (binding rows)
   double xv[G][2 * S];                 // value of every variable: structural j at j, slack k at S + k
   double yv[G][S];                     // duals of the rows
   double rr[G][S];                     // FP64 primal residuals b - A x - s
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(kPackWarps * 32) pack_kernel(TableauParams P) 
           }
         }
         bk = ld_in(P.B.b, boff + sl, dt);
-        bad |= !finite_bits(bk) || bk < 0.0;            // b_i < 0: Phase I elsewhere
+        bad |= !finite_bits(bk) || !dge(bk, -0.0);      // b_i < 0: Phase I elsewhere
         T[S - 1] = d2f_rn(bk);
         bmax = hi_mag(bk);
       }
@@ -155,7 +157,7 @@ __global__ void __launch_bounds__(kPackWarps * 32) pack_kernel(TableauParams P) 
     // The objective row: lane S-1 takes -c from the lanes holding c.
 #pragma unroll
     for (int c = 0; c < S - 1; ++c) {
-      const float v = d2f_rn(-__shfl_sync(kFull, cj, base + c));
+      const float v = -d2f_rn(__shfl_sync(kFull, cj, base + c));
       if (sl == S - 1 && c < n) T[c] = v;
     }
     // Every lane takes part in each warp-wide vote and shuffle (never behind a
@@ -248,6 +250,14 @@ __global__ void __launch_bounds__(kPackWarps * 32) pack_kernel(TableauParams P) 
     const bool solved = fits && !defer;
     if (solved && bp && sl < m) bp[sl] = bvar;
     sh.nvs[seg][sl] = nv;
+    // Compact lists for the FP64 residuals: A x needs only the basic
+    // structural columns, A^T y only the binding rows (y is zero elsewhere).
+    const unsigned below = segmask & ((1u << lane) - 1u);
+    const unsigned sb_lanes = __ballot_sync(kFull, sl < m && bvar < n) & segmask;
+    const unsigned nk_lanes = __ballot_sync(kFull, sl < S - 1 && nv >= n && nv < n + m) & segmask;
+    if (sl < m && bvar < n) sh.sbj[seg][__popc(sb_lanes & below)] = bvar;
+    if (sl < S - 1 && nv >= n && nv < n + m) sh.nsk[seg][__popc(nk_lanes & below)] = nv - n;
+    const int nsb = __popc(sb_lanes), nnk = __popc(nk_lanes);
     __syncwarp();
 
     // ---- results: plain FP32, or FP64 refinement and certificate ----
@@ -290,10 +300,11 @@ __global__ void __launch_bounds__(kPackWarps * 32) pack_kernel(TableauParams P) 
     // vector of its row.
     const double tp = P.feas_tol * (1.0 + __longlong_as_double(static_cast<long long>(bmax) << 32));
     const double td = P.feas_tol * (1.0 + __longlong_as_double(static_cast<long long>(cmax) << 32));
-    double xb = (cert && sl < m) ? double(T[S - 1]) : 0.0;          // value of the basic variable of row sl
+    const double mtp = neg_bits(tp), mtd = neg_bits(td);
+    double xb = (cert && sl < m) ? f2d_exact(T[S - 1]) : 0.0;       // value of the basic variable of row sl
     if (cert && sl < m) sh.yv[seg][sl] = 0.0;
     __syncwarp();
-    if (cert && sl < S - 1 && nv >= n && nv < n + m) sh.yv[seg][nv - n] = double(sh.objv[seg][sl]);
+    if (cert && sl < S - 1 && nv >= n && nv < n + m) sh.yv[seg][nv - n] = f2d_exact(sh.objv[seg][sl]);
     bool ok = false;
     double cx = 0.0;
     for (int round = 0; __any_sync(kFull, cert); ++round) {
@@ -310,29 +321,40 @@ __global__ void __launch_bounds__(kPackWarps * 32) pack_kernel(TableauParams P) 
       __syncwarp();
       if (cert && sl < m) sh.xv[seg][bvar < n ? bvar : S + (bvar - n)] = xb;
       __syncwarp();
-      // rows: s_i = b_i - A_i x and r_i = s_i - x_slack(i); columns: d_j = A_j^T y - c_j
+      // rows: s_i = b_i - A_i x and r_i = s_i - x_slack(i); columns: d_j = A_j^T y - c_j.
+      // (The FP64 unit is what bounds tiny LPs: sums start from -b_i and -c_j,
+      // signs flip on the bits, and the checks compare doubles as integers.)
       double sax = 0.0, dj = 0.0;
       int fail = 0;
       if (cert && sl < m) {
-        double ax = 0.0;
-        for (int j = 0; j < n; ++j) ax = fma(ld_in(P.B.A, aoff + int64_t(sl) * n + j, dt), sh.xv[seg][j], ax);
-        sax = bk - ax;
+        double nax = neg_bits(bk);                     // -(b_i - A_i x)
+        for (int q = 0; q < nsb; ++q) {
+          const int j = sh.sbj[seg][q];
+          nax = fma(ld_in(P.B.A, aoff + int64_t(sl) * n + j, dt), sh.xv[seg][j], nax);
+        }
+        sax = neg_bits(nax);
         const double r = sax - sh.xv[seg][S + sl];
         sh.rr[seg][sl] = r;
-        sh.rf[seg][sl] = float(r);
-        fail |= !(sax >= -tp) || !(sh.yv[seg][sl] >= -td) || (bvar < n && !(xb >= -tp));
+        sh.rf[seg][sl] = d2f_rn(r);
+        fail |= !dge(sax, mtp) || !dge(sh.yv[seg][sl], mtd) || (bvar < n && !dge(xb, mtp));
       }
       if (cert && sl < n) {
-        double ay = 0.0;
-        for (int k = 0; k < m; ++k) ay = fma(ld_in(P.B.A, aoff + int64_t(k) * n + sl, dt), sh.yv[seg][k], ay);
-        dj = ay - cj;
-        fail |= !(dj >= -td);
+        double ay = neg_bits(cj);
+        for (int q = 0; q < nnk; ++q) {
+          const int k = sh.nsk[seg][q];
+          ay = fma(ld_in(P.B.A, aoff + int64_t(k) * n + sl, dt), sh.yv[seg][k], ay);
+        }
+        dj = ay;
+        fail |= !dge(dj, mtd);
       }
       // duality gap c^T x = b^T y (a segment that has passed keeps its c^T x)
       const double cxr = seg_sum<S>(cert && sl < n ? cj * sh.xv[seg][sl] : 0.0);
       const double by = seg_sum<S>(cert && sl < m ? bk * sh.yv[seg][sl] : 0.0);
       if (cert) cx = cxr;
-      fail |= cert && sl == 0 && !(fabs(cx - by) <= P.feas_tol * (1.0 + fabs(cx)));
+      if (cert && sl == 0 && round > 0) {
+        const double gap = cx - by, lim = P.feas_tol * (1.0 + abs_bits(cx));
+        fail |= !dge(lim, abs_bits(gap));
+      }
       // The FP32 point itself is never accepted: the certificate bounds the
       // residuals, not the error of x (a small c_j lets x_j err by the FP32
       // rounding), so at least one correction runs first.
@@ -346,7 +368,7 @@ __global__ void __launch_bounds__(kPackWarps * 32) pack_kernel(TableauParams P) 
       // Dual: rho_i = -d_j for the basic structural j of row i; dy_k = sum_i
       // T[i][c(k)] rho_i for every non-basic slack k.
       const double djb = __shfl_sync(kFull, dj, base + (bvar < n ? bvar : 0));
-      const float rhof = (cert && sl < m && bvar < n) ? float(-djb) : 0.f;
+      const float rhof = (cert && sl < m && bvar < n) ? -d2f_rn(djb) : 0.f;
       __syncwarp();
       float dxf = 0.f;
 #pragma unroll
@@ -357,11 +379,11 @@ __global__ void __launch_bounds__(kPackWarps * 32) pack_kernel(TableauParams P) 
         sh.cs[seg][sl][c] = T[c] * rhof;
       }
       __syncwarp();
-      if (cert && sl < m) xb += double(dxf) + (bvar >= n ? sh.rr[seg][bvar - n] : 0.0);
+      if (cert && sl < m) xb += bvar >= n ? f2d_exact(dxf) + sh.rr[seg][bvar - n] : f2d_exact(dxf);
       if (cert && sl < S - 1 && nv >= n && nv < n + m) {
         float s = 0.f;
         for (int i = 0; i < m; ++i) s += sh.cs[seg][i][sl];
-        sh.yv[seg][nv - n] += double(s);
+        sh.yv[seg][nv - n] += f2d_exact(s);
       }
       __syncwarp();
     }
