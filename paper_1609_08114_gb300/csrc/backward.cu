@@ -41,6 +41,50 @@ __host__ __device__ inline BwdLayout bwd_layout(int max_m, int kmax) {
   return L;
 }
 
+// Solve the k x k system held as [M | g] (row-major, leading dimension k + 1)
+// for k <= 32 in one warp: lane r owns row r.  Gaussian elimination with
+// partial pivoting (the largest |M[r][p]|, ties to the lowest row, found on
+// the magnitude bits with integer warp reductions), one division per row and
+// step, then back substitution by columns (each lane updates its own right-
+// hand side).  FP64 is the scarce unit here, so no FP64 work is spent on
+// reductions.  Returns false (warp-uniform) if a pivot is zero.
+__device__ bool warp_solve(double *mt, int k, double *v) {
+  const int lane = threadIdx.x & 31, ld = k + 1;
+  for (int p = 0; p < k; ++p) {
+    const unsigned long long mag =
+        (lane >= p && lane < k) ? static_cast<unsigned long long>(__double_as_longlong(mt[lane * ld + p])) &
+                                      0x7fffffffffffffffull
+                                : 0ull;
+    const unsigned hi = __reduce_max_sync(kFull, unsigned(mag >> 32));
+    const unsigned lo = __reduce_max_sync(kFull, unsigned(mag >> 32) == hi ? unsigned(mag) : 0u);
+    const bool top = unsigned(mag >> 32) == hi && unsigned(mag) == lo && lane >= p && lane < k;
+    const int bk = int(__reduce_min_sync(kFull, top ? unsigned(lane) : 0xffffffffu));
+    if ((hi | lo) == 0u) return false;                 // a zero column: singular
+    if (bk != p)
+      for (int c = p + lane; c < ld; c += 32) {
+        const double t0 = mt[p * ld + c];
+        mt[p * ld + c] = mt[bk * ld + c];
+        mt[bk * ld + c] = t0;
+      }
+    __syncwarp();
+    const double piv = mt[p * ld + p];
+    if (lane > p && lane < k) {
+      const double l = mt[lane * ld + p] / piv;
+      for (int c = p + 1; c < ld; ++c) mt[lane * ld + c] = fma(-l, mt[p * ld + c], mt[lane * ld + c]);
+    }
+    __syncwarp();
+  }
+  for (int b = k - 1; b >= 0; --b) {
+    double vb = 0.0;
+    if (lane == b) vb = mt[b * ld + k] / mt[b * ld + b];
+    vb = __shfl_sync(kFull, vb, b);
+    if (lane < b) mt[lane * ld + k] = fma(-mt[lane * ld + b], vb, mt[lane * ld + k]);
+    if (lane == 0) v[b] = vb;
+    __syncwarp();
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BackwardParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
@@ -107,6 +151,14 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BackwardParams P)
       }
       if (tid == 0) s_ok = 1;
       __syncthreads();
+      if (k <= 32) {                    // small systems (the usual case): one warp
+        if (wid == 0) {
+          const bool solved = warp_solve(mt, k, vN);
+          if (lane == 0 && !solved) s_ok = 0;
+        }
+        __syncthreads();
+        if (!s_ok) ok = false;
+      } else {
       for (int p = 0; p < k; ++p) {
         // partial pivoting: the largest |mt[r][p]|, r >= p
         double bv = 1.0;     // compared as -|value| so the arg-min picks the largest
@@ -124,11 +176,16 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BackwardParams P)
             mt[bk * ld + c] = t0;
           }
         __syncthreads();
+        // One division per row for the multipliers (kept in column p, which
+        // the later steps no longer read), then the rank-1 update: FP64
+        // division is a long instruction sequence on this GPU's slow FP64 unit.
         const double piv = mt[p * ld + p];
         const int rows = k - p - 1, cols = ld - p - 1;
+        for (int r = p + 1 + tid; r < k; r += nt) mt[r * ld + p] = mt[r * ld + p] / piv;
+        __syncthreads();
         for (int idx = tid; idx < rows * cols; idx += nt) {
           const int r = p + 1 + idx / cols, c = p + 1 + idx % cols;
-          mt[r * ld + c] = fma(-(mt[r * ld + p] / piv), mt[p * ld + c], mt[r * ld + c]);
+          mt[r * ld + c] = fma(-mt[r * ld + p], mt[p * ld + c], mt[r * ld + c]);
         }
         __syncthreads();
       }
@@ -149,6 +206,7 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BackwardParams P)
         }
       } else {
         ok = false;
+      }
       }
     } else if (ok) {
       for (int b = tid; b < k; b += nt) vN[b] = 0.0;
