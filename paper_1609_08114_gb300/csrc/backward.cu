@@ -220,11 +220,19 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BackwardParams P)
     __syncthreads();
     for (int i = tid; i < m; i += nt) P.g_b[boff + i] = w[i];
     for (int j = tid; j < n; j += nt) P.g_c[coff + j] = ok ? go * P.x[coff + j] : 0.0;
+    // g_A = -w x*^T: x* is zero off the basic structurals, so the rows are
+    // written as zeros and only those k columns take an FP64 product.
     for (int i = wid; i < m; i += nw) {
-      const double wi = w[i];
       double *row = P.g_A + aoff + int64_t(i) * n;
-      for (int j = lane; j < n; j += 32) row[j] = ok ? -wi * P.x[coff + j] : 0.0;
+      for (int j = lane; j < n; j += 32) row[j] = 0.0;
     }
+    __syncthreads();
+    if (ok)
+      for (int q = wid; q < k; q += nw) {
+        const int j = slist[q];
+        const double xj = P.x[coff + j];
+        for (int i = lane; i < m; i += 32) P.g_A[aoff + int64_t(i) * n + j] = -w[i] * xj;
+      }
     __syncthreads();
   }
 }
