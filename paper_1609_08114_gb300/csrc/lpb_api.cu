@@ -128,15 +128,19 @@ lpb_err make_pass(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   if (fit_rows > rows) fit_rows = rows;
   if (o->kernel == LPB_KERNEL_SMEM && fit_rows < rows) return LPB_EUNSUPPORTED;
   if (o->kernel == LPB_KERNEL_GMEM) fit_rows = 0;
-  // With many LPs, two CTAs per SM hide more latency than shared memory saves:
-  // when the whole tableau would leave room for fewer than two CTAs per SM,
-  // every row goes to the L2 slot and the CTAs take 512 threads (two per SM).
+  // With many LPs, two CTAs per SM hide more latency than one CTA with more
+  // rows in shared memory: when the whole tableau would leave room for fewer
+  // than two CTAs per SM, the CTAs take 512 threads (two per SM) and keep in
+  // shared memory the leading rows that two CTAs per SM leave room for; the
+  // rest go to the L2 slot.
   int auto_threads_override = 0;
   if (o->kernel == LPB_KERNEL_AUTO && o->threads == 0 && b->count >= 16 * d.sms) {
     const size_t all_smem = fixed + rows * rowb;
     const int ctas = all_smem <= budget ? int(size_t(232448) / (all_smem + 1024)) : 0;
     if (ctas < 2) {
-      fit_rows = 0;
+      const size_t half = size_t(232448) / 2 - 1024 - 1024;   // per CTA, less the kernel's static shared memory
+      fit_rows = half > fixed ? (half - fixed) / rowb : 0;
+      if (fit_rows > rows) fit_rows = rows;
       auto_threads_override = 512;
     }
   }
