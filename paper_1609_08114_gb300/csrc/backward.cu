@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BackwardParams P)
     const int64_t aoff = P.B.a_off[lp], boff = P.B.b_off[lp], coff = P.B.c_off[lp];
     const double go = P.g_obj ? P.g_obj[lp] : 0.0;
     bool ok = P.status[lp] == LPB_OPTIMAL;
+    bool zeroed = false;                // the zeros of g_A are written
     // S: structural basic variables (in row order), N: rows whose slack is not basic.
     for (int i = tid; i < m; i += nt) flag[i] = 0;
     __syncthreads();
@@ -155,7 +156,13 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BackwardParams P)
         if (wid == 0) {
           const bool solved = warp_solve(mt, k, vN);
           if (lane == 0 && !solved) s_ok = 0;
+        } else {                        // meanwhile the other warps write the zeros of g_A
+          for (int i = wid - 1; i < m; i += nw - 1) {
+            double *row = P.g_A + aoff + int64_t(i) * n;
+            for (int j = lane; j < n; j += 32) row[j] = 0.0;
+          }
         }
+        zeroed = true;
         __syncthreads();
         if (!s_ok) ok = false;
       } else {
@@ -221,12 +228,15 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(BackwardParams P)
     for (int i = tid; i < m; i += nt) P.g_b[boff + i] = w[i];
     for (int j = tid; j < n; j += nt) P.g_c[coff + j] = ok ? go * P.x[coff + j] : 0.0;
     // g_A = -w x*^T: x* is zero off the basic structurals, so the rows are
-    // written as zeros and only those k columns take an FP64 product.
-    for (int i = wid; i < m; i += nw) {
-      double *row = P.g_A + aoff + int64_t(i) * n;
-      for (int j = lane; j < n; j += 32) row[j] = 0.0;
+    // written as zeros (unless that was done during the elimination) and only
+    // those k columns take an FP64 product.
+    if (!zeroed) {
+      for (int i = wid; i < m; i += nw) {
+        double *row = P.g_A + aoff + int64_t(i) * n;
+        for (int j = lane; j < n; j += 32) row[j] = 0.0;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     if (ok)
       for (int q = wid; q < k; q += nw) {
         const int j = slist[q];

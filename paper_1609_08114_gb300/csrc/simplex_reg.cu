@@ -529,19 +529,11 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
         sh.wcmax[wid] = cm;
       }
     }
-    neg = __syncthreads_or(neg);
-    if (!fits || neg) {      // the shared-memory kernel handles it (Phase I, sizes, bad data)
-      if (tid == 0) {
-        P.R.status[lp] = STATUS_PENDING;
-        list_push(P.defer_items, P.defer_count, P.list_cap, lp, P.err);
-      }
-      __syncthreads();
-      continue;
-    }
-
     // ---- the tableau: A rounded to FP32, b in column COLS-1, -c in row ROWS-1 ----
-    int bad = 0;
-    if (!warm) {
+    // (built before the block learns the checks above: one vote covers both,
+    // and an LP with some b_i < 0 or non-finite data is simply not used)
+    int bad = neg;
+    if (fits && !warm) {
     if (dt == LPB_DTYPE_F64) {
       const double *sa = reinterpret_cast<const double *>(sA);
       unsigned amax = 0u;
@@ -587,7 +579,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
         if (j < n) T[R - 1][c] = -vin_tile(sh.cin, j, dt, bad);
       }
     }
-    } else {
+    } else if (fits) {
       // Warm start: the basis of the previous objective.  Its objective row for
       // this c is r_j = sum_i c_B(i) t_ij - c_j on the non-basic columns and
       // z = sum_i c_B(i) rhs_i on the right-hand side (c of slacks is 0).
@@ -622,7 +614,7 @@ __global__ void __launch_bounds__(W * 32, reg_min_blocks<R, C, W>()) reg_kernel(
       __syncwarp();
     }
     bad = __syncthreads_or(bad);
-    if (bad) {
+    if (!fits || bad) {      // the shared-memory kernel handles it (Phase I, sizes, bad data)
       if (tid == 0) {
         P.R.status[lp] = STATUS_PENDING;
         list_push(P.defer_items, P.defer_count, P.list_cap, lp, P.err);
