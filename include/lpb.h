@@ -112,7 +112,7 @@ typedef struct {
   int32_t threads;           /* threads per CTA of the tableau kernel, a multiple of 32 up to 1024 [auto] */
   int32_t reg_warps;         /* warps per LP of the register kernel: 1 (m, n <= 31), 4 or 8
                                 [autotuned, else 1 when every LP has m, n <= 31, else 8; with
-                                kernel = AUTO and reg_warps = 0, batches of LPs with m, n <= 15
+                                kernel = AUTO and reg_warps = 0, batches of LPs with m, n <= 31
                                 take the several-LPs-per-warp kernel (LPB_KERNEL_PACK)] */
   int32_t pivot_rule;        /* lpb_pivot_rule: Step 1's entering-column rule [LPB_PIVOT_LPC] */
   uint64_t seed;             /* LPB_PIVOT_RPC: seed of the counter-based random draw [0] */
@@ -146,9 +146,9 @@ typedef enum {
   LPB_KERNEL_SMEM = 1,   /* tableau in shared memory, one CTA per LP */
   LPB_KERNEL_GMEM = 2,   /* tableau in a per-CTA workspace slot (L2 resident) */
   LPB_KERNEL_REG = 3,    /* tableau in registers (FP32, m < 128, type 1) */
-  LPB_KERNEL_PACK = 4    /* several tiny LPs per warp: 4 (m, n <= 7) or 2 (m, n <= 15)
-                            register tableaux in one warp (FP32 modes, largest-coefficient
-                            or random rule) */
+  LPB_KERNEL_PACK = 4    /* several tiny LPs per warp: 4 (m, n <= 7), 2 (m, n <= 15) or 1
+                            (m, n <= 31) register tableaux in one warp (FP32 modes,
+                            largest-coefficient or random rule) */
 } lpb_kernel;
 
 typedef struct lpb_handle lpb_handle;

@@ -230,8 +230,9 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   lpb_options og = *o;          // options of the shared-memory / L2-slot kernel passes
   if (og.kernel == LPB_KERNEL_REG) { og.kernel = LPB_KERNEL_AUTO; og.threads = 0; }
   int np = 0;
-  // Several tiny LPs per warp: asked for, or the default for batches of LPs
-  // with m, n <= 15 when no register-kernel shape is asked for.
+  // Several tiny LPs per warp (one per warp up to 31): asked for, or the
+  // default for batches of LPs with m, n <= 31 when no register-kernel shape is
+  // asked for.
   const int lanes = (fp32 && !se) ? pack_lanes(b->max_m, b->max_n) : 0;
   if (o->kernel == LPB_KERNEL_PACK && lanes == 0) return LPB_EUNSUPPORTED;
   if (lanes > 0 && (o->kernel == LPB_KERNEL_PACK ||

@@ -1,6 +1,7 @@
 // simplex_pack.cu -- several tiny LPs per warp: the FP32 register tableau of
 // an LP with m, n <= S - 1 lives in a segment of S lanes (S = 8: four LPs per
-// warp; S = 16: two), with the FP64 refinement and certificate fused in.
+// warp; S = 16: two; S = 32: one), with the FP64 refinement and certificate
+// fused in.
 //
 // Section 3.1 Steps 1-3 in the compact (exchange) tableau of each LP.  Lane
 // i < S - 1 of a segment holds constraint row i, lane S - 1 the objective row
@@ -37,11 +38,13 @@ struct PackWarp {
   int nvs[G][S];                       // variable of each non-basic column
   int sbj[G][S];                       // the basic structural variables (their column of A)
   int nsk[G][S];                       // the rows whose slack is non-basic (binding rows)
+  int nsc[G][S];                       // ... and the tableau column of that slack
   double xv[G][2 * S];                 // value of every variable: structural j at j, slack k at S + k
   double yv[G][S];                     // duals of the rows
   double rr[G][S];                     // FP64 primal residuals b - A x - s
   float rf[G][S];                      // the same in FP32
-  float cs[G][S][S + 1];               // products T[i][c] rho_i for the dual correction's column sums
+  float tf[G][S][S + 1];               // the final FP32 tableau, row sl of segment seg at tf[seg][sl]
+  float rh[G][S];                      // FP32 dual residual rho_i of each row
 };
 
 // Butterfly arg-min over the S lanes of a segment: (value, key) order with the
@@ -256,7 +259,17 @@ __global__ void __launch_bounds__(kPackWarps * 32) pack_kernel(TableauParams P) 
     const unsigned sb_lanes = __ballot_sync(kFull, sl < m && bvar < n) & segmask;
     const unsigned nk_lanes = __ballot_sync(kFull, sl < S - 1 && nv >= n && nv < n + m) & segmask;
     if (sl < m && bvar < n) sh.sbj[seg][__popc(sb_lanes & below)] = bvar;
-    if (sl < S - 1 && nv >= n && nv < n + m) sh.nsk[seg][__popc(nk_lanes & below)] = nv - n;
+    if (sl < S - 1 && nv >= n && nv < n + m) {
+      sh.nsk[seg][__popc(nk_lanes & below)] = nv - n;
+      sh.nsc[seg][__popc(nk_lanes & below)] = sl;
+    }
+    // The refinement reads the final tableau from shared memory with runtime
+    // indices: its loops then stay rolled (the unrolled register form of every
+    // S-wide loop made the code outgrow the instruction cache at S = 32).
+    if (refine) {
+#pragma unroll
+      for (int c = 0; c < S; ++c) sh.tf[seg][sl][c] = T[c];
+    }
     const int nsb = __popc(sb_lanes), nnk = __popc(nk_lanes);
     __syncwarp();
 
@@ -368,21 +381,16 @@ __global__ void __launch_bounds__(kPackWarps * 32) pack_kernel(TableauParams P) 
       // Dual: rho_i = -d_j for the basic structural j of row i; dy_k = sum_i
       // T[i][c(k)] rho_i for every non-basic slack k.
       const double djb = __shfl_sync(kFull, dj, base + (bvar < n ? bvar : 0));
-      const float rhof = (cert && sl < m && bvar < n) ? -d2f_rn(djb) : 0.f;
+      sh.rh[seg][sl] = (cert && sl < m && bvar < n) ? -d2f_rn(djb) : 0.f;
       __syncwarp();
-      float dxf = 0.f;
-#pragma unroll
-      for (int c = 0; c < S - 1; ++c) {
-        const int v = sh.nvs[seg][c];
-        const float rk = (v >= n && v < n + m) ? sh.rf[seg][v - n] : 0.f;
-        dxf = fmaf(T[c], rk, dxf);
-        sh.cs[seg][sl][c] = T[c] * rhof;
+      if (cert && sl < m) {
+        float dxf = 0.f;
+        for (int q = 0; q < nnk; ++q) dxf = fmaf(sh.tf[seg][sl][sh.nsc[seg][q]], sh.rf[seg][sh.nsk[seg][q]], dxf);
+        xb += bvar >= n ? f2d_exact(dxf) + sh.rr[seg][bvar - n] : f2d_exact(dxf);
       }
-      __syncwarp();
-      if (cert && sl < m) xb += bvar >= n ? f2d_exact(dxf) + sh.rr[seg][bvar - n] : f2d_exact(dxf);
       if (cert && sl < S - 1 && nv >= n && nv < n + m) {
         float s = 0.f;
-        for (int i = 0; i < m; ++i) s += sh.cs[seg][i][sl];
+        for (int i = 0; i < m; ++i) s = fmaf(sh.tf[seg][i][sl], sh.rh[seg][i], s);
         sh.yv[seg][nv - n] += f2d_exact(s);
       }
       __syncwarp();
@@ -408,23 +416,27 @@ __global__ void __launch_bounds__(kPackWarps * 32) pack_kernel(TableauParams P) 
 }  // namespace
 
 // Lanes per LP for batches whose LPs all have m, n <= max_m, max_n: 8 (four
-// LPs per warp) up to 7, 16 (two per warp) up to 15; 0 when none fits.
+// LPs per warp) up to 7, 16 (two per warp) up to 15, 32 (one) up to 31; 0 when
+// none fits.
 int pack_lanes(int max_m, int max_n) {
   if (max_m <= 7 && max_n <= 7) return 8;
   if (max_m <= 15 && max_n <= 15) return 16;
+  if (max_m <= 31 && max_n <= 31) return 32;
   return 0;
 }
 
 cudaError_t pack_occupancy(int lanes, int *ctas, int *threads) {
   *threads = kPackWarps * 32;
   const void *fn = lanes == 8 ? reinterpret_cast<const void *>(&pack_kernel<8>)
-                              : reinterpret_cast<const void *>(&pack_kernel<16>);
+                 : lanes == 16 ? reinterpret_cast<const void *>(&pack_kernel<16>)
+                               : reinterpret_cast<const void *>(&pack_kernel<32>);
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, *threads, 0);
 }
 
 cudaError_t launch_pack(const TableauParams &p, int lanes, int grid, cudaStream_t s) {
   if (lanes == 8) pack_kernel<8><<<grid, kPackWarps * 32, 0, s>>>(p);
   else if (lanes == 16) pack_kernel<16><<<grid, kPackWarps * 32, 0, s>>>(p);
+  else if (lanes == 32) pack_kernel<32><<<grid, kPackWarps * 32, 0, s>>>(p);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }

@@ -70,11 +70,12 @@ def test_one_warp_templates(solver, m, n, prec, rtol):
 
 
 @pytest.mark.parametrize("m,n", [(1, 1), (2, 7), (7, 2), (5, 5), (7, 7), (8, 8), (7, 8), (8, 3), (12, 15), (15, 15),
-                                 (15, 9)])
+                                 (15, 9), (16, 16), (16, 3), (20, 31), (31, 7), (31, 31)])
 @pytest.mark.parametrize("prec,rtol", [("fp32_refine", 1e-8), ("fp32", 1e-5)])
 def test_several_lps_per_warp(solver, m, n, prec, rtol):
-    """Several tiny LPs per warp (four of m, n <= 7 or two of m, n <= 15 in one warp), at and
-    near both segment limits and with a ragged last group (1001 LPs), against the oracle."""
+    """Several tiny LPs per warp (four of m, n <= 7, two of m, n <= 15, one of m, n <= 31 in
+    one warp), at and near every segment limit and with a ragged last group (1001 LPs),
+    against the oracle."""
     from paper_1609_08114_gb300 import KERNEL_PACK
     sb = synth.type1(1001, m, n, seed=31 * m + n)
     got = run(solver, sb, prec, kernel=KERNEL_PACK)
