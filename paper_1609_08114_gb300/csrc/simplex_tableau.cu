@@ -135,34 +135,34 @@ template <> struct Vec<double> {
   using type = double2;
   static constexpr int N = 2;
 };
-// One vector of a row under Step 3: x - f pr, with component ce (the pivot
-// column, -1 if none) set to -f; and the scaled pivot row pr * rp with
-// component ce set to rp.  Vectors pass by value (taking a vector's address
-// would move it to local memory).
-__device__ __forceinline__ float4 upd_vec(float4 x, float4 pr, float nf, int ce) {
-  x.x = ce == 0 ? nf : fmaf(nf, pr.x, x.x);
-  x.y = ce == 1 ? nf : fmaf(nf, pr.y, x.y);
-  x.z = ce == 2 ? nf : fmaf(nf, pr.z, x.z);
-  x.w = ce == 3 ? nf : fmaf(nf, pr.w, x.w);
+// One vector of a row under Step 3: x - f pr; and the scaled pivot row
+// pr * rp.  (The pivot column itself is set afterwards, once per row, so the
+// update of every other element carries no test for it.)  Vectors pass by
+// value (taking a vector's address would move it to local memory).
+__device__ __forceinline__ float4 upd_vec(float4 x, float4 pr, float nf) {
+  x.x = fmaf(nf, pr.x, x.x);
+  x.y = fmaf(nf, pr.y, x.y);
+  x.z = fmaf(nf, pr.z, x.z);
+  x.w = fmaf(nf, pr.w, x.w);
   return x;
 }
-__device__ __forceinline__ double2 upd_vec(double2 x, double2 pr, double nf, int ce) {
-  x.x = ce == 0 ? nf : fma(nf, pr.x, x.x);
-  x.y = ce == 1 ? nf : fma(nf, pr.y, x.y);
+__device__ __forceinline__ double2 upd_vec(double2 x, double2 pr, double nf) {
+  x.x = fma(nf, pr.x, x.x);
+  x.y = fma(nf, pr.y, x.y);
   return x;
 }
-__device__ __forceinline__ float4 scale_vec(float4 pr, float rp, int ce) {
-  return make_float4(ce == 0 ? rp : pr.x * rp, ce == 1 ? rp : pr.y * rp, ce == 2 ? rp : pr.z * rp,
-                     ce == 3 ? rp : pr.w * rp);
+__device__ __forceinline__ float4 scale_vec(float4 pr, float rp) {
+  return make_float4(pr.x * rp, pr.y * rp, pr.z * rp, pr.w * rp);
 }
-__device__ __forceinline__ double2 scale_vec(double2 pr, double rp, int ce) {
-  return make_double2(ce == 0 ? rp : pr.x * rp, ce == 1 ? rp : pr.y * rp);
+__device__ __forceinline__ double2 scale_vec(double2 pr, double rp) {
+  return make_double2(pr.x * rp, pr.y * rp);
 }
 
 // Step 3 on the calling warp's rows: with rp = 1 / t_le, every row i != l
 // becomes row_i - (t_ie rp) row_l and its column e -t_ie rp; the warp owning
 // row l writes the scaled row (rp at column e) to S.rowb instead of row l, so
 // that other warps can still read the old row; pivot_finish() copies it.
+// Column e is written by a scalar pass after the vector sweep.
 // Lanes own 16-byte vectors of columns; a lane keeps its vector of the pivot
 // row in registers and loads kQ rows of its column before it stores any, so a
 // batch costs one round trip to shared memory or L2.
@@ -179,13 +179,11 @@ __device__ __forceinline__ void pivot_update(const Tab<T> &S_, int rows, int l, 
   if (r0 >= r1) return;
   const bool own_l = l >= r0 && l < r1;
   const int nv = (S.nc + NV) / NV;        // vectors holding columns 0..nc
-  const int ev = e / NV, ec = e % NV;
   const V *prow = reinterpret_cast<const V *>(S.row(l));
   V *rowb = reinterpret_cast<V *>(S.rowb);
   for (int jv = lane; jv < nv; jv += 32) {
     const V pr = prow[jv];
-    const int ce = jv == ev ? ec : -1;
-    if (own_l) rowb[jv] = scale_vec(pr, rp, ce);
+    if (own_l) rowb[jv] = scale_vec(pr, rp);
     for (int i0 = r0; i0 < r1; i0 += kQ) {
       V v[kQ];
       T f[kQ];
@@ -202,11 +200,15 @@ __device__ __forceinline__ void pivot_update(const Tab<T> &S_, int rows, int l, 
       for (int q = 0; q < kQ; ++q) {
         const int i = i0 + q;
         if (i >= r1 || i == l) continue;
-        const V x = upd_vec(v[q], pr, -f[q], ce);
+        const V x = upd_vec(v[q], pr, -f[q]);
         rw[q][jv] = x;
       }
     }
   }
+  __syncwarp();                           // the vector stores of this warp's rows are done
+  for (int i = r0 + lane; i < r1; i += 32)
+    if (i != l) S.at(i, e) = -S.colb[i];
+  if (own_l && lane == 0) S.rowb[e] = rp;
 }
 
 // After the barrier that follows pivot_update: the owner of row l copies the
