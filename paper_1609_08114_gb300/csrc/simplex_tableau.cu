@@ -162,11 +162,12 @@ __device__ __forceinline__ double2 scale_vec(double2 pr, double rp) {
 // becomes row_i - (t_ie rp) row_l and its column e -t_ie rp; the warp owning
 // row l writes the scaled row (rp at column e) to S.rowb instead of row l, so
 // that other warps can still read the old row; pivot_finish() copies it.
-// Column e is written by a scalar pass after the vector sweep.
-// Lanes own 16-byte vectors of columns; a lane keeps its vector of the pivot
-// row in registers and loads kQ rows of its column before it stores any, so a
-// batch costs one round trip to shared memory or L2.
-template <typename T, int kQ>
+// Lanes own 16-byte vectors of columns, kJ per lane per chunk of 32 kJ
+// vectors: a lane keeps its vectors of the pivot row in registers while the
+// warp's rows stream past, so each row's multiplier and address are read once
+// per chunk and the kJ loads of a row are in flight together.  Column e is
+// written by a scalar pass after the vector sweep.
+template <typename T, int kJ>
 __device__ __forceinline__ void pivot_update(const Tab<T> &S_, int rows, int l, int e, T rp) {
   const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
   using V = typename Vec<T>::type;
@@ -181,28 +182,26 @@ __device__ __forceinline__ void pivot_update(const Tab<T> &S_, int rows, int l, 
   const int nv = (S.nc + NV) / NV;        // vectors holding columns 0..nc
   const V *prow = reinterpret_cast<const V *>(S.row(l));
   V *rowb = reinterpret_cast<V *>(S.rowb);
-  for (int jv = lane; jv < nv; jv += 32) {
-    const V pr = prow[jv];
-    if (own_l) rowb[jv] = scale_vec(pr, rp);
-    for (int i0 = r0; i0 < r1; i0 += kQ) {
-      V v[kQ];
-      T f[kQ];
-      V *rw[kQ];
+  for (int j0 = lane; j0 < nv; j0 += 32 * kJ) {
+    // Vectors past the row's end stand in as j0 (loaded, never stored).
+    int jj[kJ];
+    V pr[kJ];
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) {
-        const int i = i0 + q;
-        const bool ok = i < r1 && i != l;
-        f[q] = ok ? S.colb[i] : T(0);
-        rw[q] = reinterpret_cast<V *>(S.row(ok ? i : r0));
-        v[q] = rw[q][jv];                 // row r0 stands in for a skipped row
-      }
+    for (int k = 0; k < kJ; ++k) {
+      jj[k] = j0 + 32 * k < nv ? j0 + 32 * k : j0;
+      pr[k] = prow[jj[k]];
+      if (own_l && j0 + 32 * k < nv) rowb[jj[k]] = scale_vec(pr[k], rp);
+    }
+    for (int i = r0; i < r1; ++i) {
+      if (i == l) continue;
+      const T nf = -S.colb[i];
+      V *rw = reinterpret_cast<V *>(S.row(i));
+      V v[kJ];
 #pragma unroll
-      for (int q = 0; q < kQ; ++q) {
-        const int i = i0 + q;
-        if (i >= r1 || i == l) continue;
-        const V x = upd_vec(v[q], pr, -f[q]);
-        rw[q][jv] = x;
-      }
+      for (int k = 0; k < kJ; ++k) v[k] = rw[jj[k]];
+#pragma unroll
+      for (int k = 0; k < kJ; ++k)
+        if (j0 + 32 * k < nv) rw[jj[k]] = upd_vec(v[k], pr[k], nf);
     }
   }
   __syncwarp();                           // the vector stores of this warp's rows are done
@@ -232,7 +231,7 @@ __device__ __forceinline__ void pivot_finish(const Tab<T> &S_, int rows, int l) 
 template <typename T>
 __device__ __forceinline__ void update_any(const Tab<T> &S_, int rows, int l, int e, T rp) {
   const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
-  pivot_update<T, sizeof(T) == 4 ? 4 : 2>(S, rows, l, e, rp);
+  pivot_update<T, sizeof(T) == 4 ? 3 : 2>(S, rows, l, e, rp);
 }
 
 // A whole pivot on (l, e) for the callers outside the Step 1-3 loop (Phase-I
