@@ -146,9 +146,12 @@ typedef enum {
   LPB_KERNEL_SMEM = 1,   /* tableau in shared memory, one CTA per LP */
   LPB_KERNEL_GMEM = 2,   /* tableau in a per-CTA workspace slot (L2 resident) */
   LPB_KERNEL_REG = 3,    /* tableau in registers (FP32, m < 128, type 1) */
-  LPB_KERNEL_PACK = 4    /* several tiny LPs per warp: 4 (m, n <= 7), 2 (m, n <= 15) or 1
+  LPB_KERNEL_PACK = 4,   /* several tiny LPs per warp: 4 (m, n <= 7), 2 (m, n <= 15) or 1
                             (m, n <= 31) register tableaux in one warp (FP32 modes,
                             largest-coefficient or random rule) */
+  LPB_KERNEL_WARP = 5    /* one warp per LP, the FP32 tableau in shared memory (FP64 input,
+                            m, n <= 127; FP32 modes, largest-coefficient or random rule; no
+                            warm starts in lpb_solve_shared) */
 } lpb_kernel;
 
 typedef struct lpb_handle lpb_handle;

@@ -20,11 +20,11 @@ import torch
 
 from . import _lib
 from ._lib import (BAD_SIZE, FP32, FP32_REFINE, FP64, INFEASIBLE, ITER_LIMIT, KERNEL_AUTO, KERNEL_GMEM,
-                   KERNEL_PACK, KERNEL_REG, KERNEL_SMEM, NUMERIC, OPTIMAL, UNBOUNDED, LPBError)
+                   KERNEL_PACK, KERNEL_REG, KERNEL_SMEM, KERNEL_WARP, NUMERIC, OPTIMAL, UNBOUNDED, LPBError)
 
 __all__ = ["Solver", "LPBatch", "SolveResult", "LPBError", "OPTIMAL", "INFEASIBLE", "UNBOUNDED",
            "ITER_LIMIT", "NUMERIC", "BAD_SIZE", "FP64", "FP32_REFINE", "FP32", "KERNEL_AUTO",
-           "KERNEL_SMEM", "KERNEL_GMEM", "KERNEL_REG", "KERNEL_PACK", "PRECISIONS"]
+           "KERNEL_SMEM", "KERNEL_GMEM", "KERNEL_REG", "KERNEL_PACK", "KERNEL_WARP", "PRECISIONS"]
 
 PRECISIONS = {"fp64": FP64, "fp32_refine": FP32_REFINE, "fp32": FP32}
 # Step 1 rules of Section 4.2: most negative reduced cost, or a random eligible column.

@@ -21,7 +21,7 @@ FP64, FP32_REFINE, FP32 = 0, 1, 2
 # lpb_dtype
 DTYPE_F32, DTYPE_F64 = 0, 1
 # lpb_kernel
-KERNEL_AUTO, KERNEL_SMEM, KERNEL_GMEM, KERNEL_REG, KERNEL_PACK = 0, 1, 2, 3, 4
+KERNEL_AUTO, KERNEL_SMEM, KERNEL_GMEM, KERNEL_REG, KERNEL_PACK, KERNEL_WARP = 0, 1, 2, 3, 4, 5
 # lpb_pivot_rule
 PIVOT_LPC, PIVOT_RPC, PIVOT_STEEPEST = 0, 1, 2
 

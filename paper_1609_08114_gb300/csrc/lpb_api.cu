@@ -68,6 +68,7 @@ struct Pass {
   int kcap = 0, mode = MODE_FP64, grid = 0, threads = 128;
   int reg = -1;              // >= 0: register-resident kernel configuration
   int pack = 0;              // > 0: several LPs per warp, this many lanes per LP
+  bool warp = false;         // one warp per LP, the tableau in shared memory
   int list = LIST_ALL, cls = 0;
   int lim_m = 0, lim_n = 0;  // size bounds of the launch
   int group = 0;             // timing group: 0 first solve, 1 Phase-I pass, 2 FP64 re-solve
@@ -199,6 +200,23 @@ lpb_err pack_pass(const DeviceInfo &d, const lpb_batch *b, int lanes, int mode, 
   return LPB_OK;
 }
 
+lpb_err warp_pass(const DeviceInfo &d, const lpb_batch *b, int mode, Pass *p) {
+  int occ = 0;
+  if (warp_occupancy(b->max_m, b->max_n, &occ, &p->threads, &p->smem) != cudaSuccess) return LPB_ECUDA;
+  if (occ < 1 || p->smem > d.smem_optin) return LPB_EUNSUPPORTED;
+  p->fp64 = false;
+  p->mode = mode;
+  p->warp = true;
+  p->lim_m = b->max_m;
+  p->lim_n = b->max_n;
+  // Each warp takes one LP at a time: no more CTAs than groups of LPs.
+  const long long warps_per_cta = p->threads / 32;
+  const long long need = (static_cast<long long>(b->count) + warps_per_cta - 1) / warps_per_cta;
+  p->grid = occ * d.sms;
+  if (need < p->grid) p->grid = int(need > 0 ? need : 1);
+  return LPB_OK;
+}
+
 lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o, bool basis_given,
                   Plan *pl) {
   if (!b || !o) return LPB_EINVAL;
@@ -209,7 +227,7 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   if (o->max_iter < 0 || o->eps_p < 0 || o->eps_d < 0 || o->feas_tol < 0) return LPB_EINVAL;
   if (o->pivot_rule != LPB_PIVOT_LPC && o->pivot_rule != LPB_PIVOT_RPC && o->pivot_rule != LPB_PIVOT_STEEPEST)
     return LPB_EINVAL;
-  if (o->kernel < LPB_KERNEL_AUTO || o->kernel > LPB_KERNEL_PACK) return LPB_EINVAL;
+  if (o->kernel < LPB_KERNEL_AUTO || o->kernel > LPB_KERNEL_WARP) return LPB_EINVAL;
   // Steepest edge has register-kernel instantiations for the 8-warp templates only.
   const bool se = o->pivot_rule == LPB_PIVOT_STEEPEST;
   const bool fp32 = o->prec != LPB_FP64;
@@ -243,6 +261,16 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
     np = 1;
   }
   if (og.kernel == LPB_KERNEL_PACK) { og.kernel = LPB_KERNEL_AUTO; og.threads = 0; }
+  // One warp per LP with the tableau in shared memory: asked for.
+  if (o->kernel == LPB_KERNEL_WARP) {
+    if (!fp32 || se || b->dtype != LPB_DTYPE_F64 || !warp_fits(b->max_m, b->max_n)) return LPB_EUNSUPPORTED;
+    Pass &p = pl->pass[0];
+    if ((e = warp_pass(d, b, mode, &p)) != LPB_OK) return e;
+    p.list = LIST_ALL;
+    np = 1;
+    og.kernel = LPB_KERNEL_AUTO;
+    og.threads = 0;
+  }
   if (np == 0 && fp32 && o->kernel == LPB_KERNEL_AUTO && !uniform) {
     // Size classes: the register-tableau templates with `want_w` warps in
     // increasing size, then the shared-memory / L2-slot kernel for the rest.
@@ -457,6 +485,7 @@ lpb_err run_solve(const DeviceInfo &d, int32_t *ctr, uint32_t *err, const lpb_ba
         break;
     }
     const cudaError_t ce = ps.pack > 0 ? launch_pack(p, ps.pack, ps.grid, s)
+                         : ps.warp ? launch_warp(p, ps.grid, ps.threads, ps.smem, s)
                          : ps.reg >= 0 ? launch_reg(p, ps.reg, ps.grid, ps.smem, s)
                                        : launch_tableau(p, ps.fp64, ps.grid, ps.threads, ps.smem, s);
     if (ce != cudaSuccess) return LPB_ECUDA;
@@ -1114,7 +1143,8 @@ lpb_err lpb_autotune(lpb_handle *h, const lpb_batch *b, const lpb_options *o, co
       {LPB_KERNEL_AUTO, 0, fp32 ? 8 : 0}, {LPB_KERNEL_AUTO, 0, fp32 ? 4 : 0}, {LPB_KERNEL_AUTO, 0, fp32 ? 1 : 0},
       {LPB_KERNEL_AUTO, 256, fp32 ? 8 : 0},
       {LPB_KERNEL_AUTO, 512, fp32 ? 8 : 0}, {LPB_KERNEL_AUTO, 1024, fp32 ? 8 : 0}, {LPB_KERNEL_SMEM, 0, 0},
-      {LPB_KERNEL_GMEM, 0, 0}, {fp32 ? LPB_KERNEL_PACK : LPB_KERNEL_AUTO, 0, 0}};
+      {LPB_KERNEL_GMEM, 0, 0}, {fp32 ? LPB_KERNEL_PACK : LPB_KERNEL_AUTO, 0, 0},
+      {fp32 ? LPB_KERNEL_WARP : LPB_KERNEL_AUTO, 0, 0}};
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return LPB_ECUDA;

@@ -214,6 +214,61 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Bulk prefetch of [p, p + bytes) into L2, shrunk to whole 16-byte units
+// inside the range; a hint with no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
+  const uintptr_t lo = (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15);
+  const uintptr_t hi = (reinterpret_cast<uintptr_t>(p) + bytes) & ~uintptr_t(15);
+  if (hi > lo && hi - lo < (uintptr_t(1) << 31))
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(lo), "r"(unsigned(hi - lo)) : "memory");
+}
+
+// FP64 -> FP32 round to nearest even on the integer bits, without branches.
+// Magnitudes below the smallest normal float become a signed zero; magnitudes
+// that round beyond the float range, infinities and NaNs set `bad`.
+__device__ __forceinline__ float d2f_tile(double d, int &bad) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(d));
+  const unsigned hi = unsigned(u >> 32), lo = unsigned(u);
+  const unsigned ahi = hi & 0x7fffffffu;
+  unsigned f = ((ahi - (896u << 20)) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  f += unsigned(rem > 0x10000000u) | (unsigned(rem == 0x10000000u) & f);
+  const bool normal = ahi >= (897u << 20);
+  bad |= int(ahi >= (1151u << 20)) | int(normal & (f >= 0x7f800000u));
+  return __uint_as_float((hi & 0x80000000u) | (normal ? f : 0u));
+}
+
+// FP64 -> FP32 by truncation on the integer bits (relative error below 2^-23,
+// the FP32 tableau's own precision; the refinement works with the exact A):
+// magnitudes below the smallest normal float become a signed zero.  `amax`
+// keeps the largest high word of |d| seen, so that one test afterwards
+// catches values beyond the float range, infinities and NaNs.
+__device__ __forceinline__ float d2f_trunc(double d, unsigned &amax) {
+  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(d));
+  const unsigned hi = unsigned(u >> 32), lo = unsigned(u);
+  const unsigned ahi = hi & 0x7fffffffu;
+  amax = max(amax, ahi);
+  const unsigned f = __funnelshift_l(lo, ahi - (896u << 20), 3);   // ((ahi - bias) << 3) | (lo >> 29)
+  return __uint_as_float((hi & 0x80000000u) | (ahi >= (897u << 20) ? f : 0u));
+}
+
+// A double's high word as a float, truncated to 20 mantissa bits (relative
+// error below 2^-20), in integer operations: magnitudes below the float range
+// give 0, above it infinity.  Used where FP32 accuracy is ample (products with
+// the small refinement corrections).
+__device__ __forceinline__ float hi2f(unsigned hi) {
+  const unsigned ahi = hi & 0x7fffffffu;
+  const unsigned f = ahi < (897u << 20) ? 0u : (ahi >= (1151u << 20) ? 0x7f800000u : ((ahi - (896u << 20)) << 3));
+  return __uint_as_float((hi & 0x80000000u) | f);
+}
+
+// Approximate reciprocal (one special-function-unit instruction, about 1 ulp).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // ---- bulk asynchronous copies (TMA engine) and transaction mbarriers ------
 //
 // A bulk copy needs 16-byte aligned source and destination and a size that is
@@ -367,6 +422,12 @@ cudaError_t launch_reg(const TableauParams &p, int cfg, int grid, size_t smem, c
 int pack_lanes(int max_m, int max_n);
 cudaError_t pack_occupancy(int lanes, int *ctas, int *threads);
 cudaError_t launch_pack(const TableauParams &p, int lanes, int grid, cudaStream_t s);
+// One warp per LP, the tableau in shared memory (simplex_warp.cu): whether LPs
+// up to max_m x max_n fit (m, n <= 127), warps per CTA, shared memory and
+// CTAs per SM, and the launch.
+bool warp_fits(int max_m, int max_n);
+cudaError_t warp_occupancy(int max_m, int max_n, int *ctas, int *threads, size_t *smem);
+cudaError_t launch_warp(const TableauParams &p, int grid, int threads, size_t smem, cudaStream_t s);
 size_t hyperbox_smem_bytes(int n, int elem_bytes, bool shared_box);
 cudaError_t launch_hyperbox(const HyperboxParams &p, uint32_t *err, cudaStream_t s);
 // Backward kernel (backward.cu).

@@ -85,15 +85,6 @@ constexpr int kBad = 1 << 30;   // a key larger than any real key
 constexpr int kShareChunk = 16;
 constexpr int kWarmMax = 32;
 
-// Bulk prefetch of [p, p + bytes) into L2, shrunk to whole 16-byte units
-// inside the range; a hint with no completion to wait for.
-__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes) {
-  const uintptr_t lo = (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15);
-  const uintptr_t hi = (reinterpret_cast<uintptr_t>(p) + bytes) & ~uintptr_t(15);
-  if (hi > lo && hi - lo < (uintptr_t(1) << 31))
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(lo), "r"(unsigned(hi - lo)) : "memory");
-}
-
 // Prefetch A, b and c of an LP into L2 when it fits the launch.
 __device__ __forceinline__ void prefetch_lp(const TableauParams &P, int m, int n, long long aoff, long long boff,
                                             long long coff) {
@@ -166,35 +157,6 @@ __host__ __device__ inline int a_stride(int max_n, int es) {
   return s * per;
 }
 
-// FP64 -> FP32 round to nearest even on the integer bits, without branches.
-// Magnitudes below the smallest normal float become a signed zero; magnitudes
-// that round beyond the float range, infinities and NaNs set `bad`.
-__device__ __forceinline__ float d2f_tile(double d, int &bad) {
-  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(d));
-  const unsigned hi = unsigned(u >> 32), lo = unsigned(u);
-  const unsigned ahi = hi & 0x7fffffffu;
-  unsigned f = ((ahi - (896u << 20)) << 3) | (lo >> 29);
-  const unsigned rem = lo & 0x1fffffffu;
-  f += unsigned(rem > 0x10000000u) | (unsigned(rem == 0x10000000u) & f);
-  const bool normal = ahi >= (897u << 20);
-  bad |= int(ahi >= (1151u << 20)) | int(normal & (f >= 0x7f800000u));
-  return __uint_as_float((hi & 0x80000000u) | (normal ? f : 0u));
-}
-
-// FP64 -> FP32 by truncation on the integer bits (relative error below 2^-23,
-// the FP32 tableau's own precision; the refinement works with the exact A):
-// magnitudes below the smallest normal float become a signed zero.  `amax`
-// keeps the largest high word of |d| seen, so that one test afterwards
-// catches values beyond the float range, infinities and NaNs.
-__device__ __forceinline__ float d2f_trunc(double d, unsigned &amax) {
-  const unsigned long long u = static_cast<unsigned long long>(__double_as_longlong(d));
-  const unsigned hi = unsigned(u >> 32), lo = unsigned(u);
-  const unsigned ahi = hi & 0x7fffffffu;
-  amax = max(amax, ahi);
-  const unsigned f = __funnelshift_l(lo, ahi - (896u << 20), 3);   // ((ahi - bias) << 3) | (lo >> 29)
-  return __uint_as_float((hi & 0x80000000u) | (ahi >= (897u << 20) ? f : 0u));
-}
-
 // Smallest power of two >= k (1 <= k <= 32).
 __host__ __device__ constexpr int pow2_at_least(int k) { return k <= 1 ? 1 : 2 * pow2_at_least((k + 1) / 2); }
 
@@ -228,23 +190,6 @@ __device__ __forceinline__ float vin_tile(const double *v, int i, int dt, int &b
   const float f = reinterpret_cast<const float *>(v)[i];
   bad |= !isfinite(f);
   return f;
-}
-
-// A double's high word as a float, truncated to 20 mantissa bits (relative
-// error below 2^-20), in integer operations: magnitudes below the float range
-// give 0, above it infinity.  Used where FP32 accuracy is ample (products with
-// the small refinement corrections).
-__device__ __forceinline__ float hi2f(unsigned hi) {
-  const unsigned ahi = hi & 0x7fffffffu;
-  const unsigned f = ahi < (897u << 20) ? 0u : (ahi >= (1151u << 20) ? 0x7f800000u : ((ahi - (896u << 20)) << 3));
-  return __uint_as_float((hi & 0x80000000u) | f);
-}
-
-// Approximate reciprocal (one special-function-unit instruction, about 1 ulp).
-__device__ __forceinline__ float rcp_approx(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
 }
 
 template <typename T>

@@ -1,0 +1,912 @@
+// simplex_warp.cu -- one warp per LP, the compact FP32 tableau in shared
+// memory, FP64 refinement and certificate fused in (FP64 input, LPs with
+// m, n <= 127 whose slack basis is feasible).
+//
+// Section 3.1 Steps 1-3 on the compact (exchange) tableau, with the paper's
+// Section 4.1 "one block per LP" narrowed to one warp per LP: the warps of a
+// CTA share nothing but the CTA's shared memory, so a solve has no block
+// barrier at all.  At m = n = 100 a tableau is 101 x 108 floats (43.6 KB), so
+// an SM holds five LPs at once.  Design:
+//
+//   * Layout: row i of the tableau (rows 0..m-1 the constraints, row m the
+//     objective row, column n the right-hand side) starts at i * S floats.
+//     The stride S is a multiple of 4 with S / 4 odd, so that the eight rows a
+//     quarter-warp touches in one 16-byte access fall in eight disjoint groups
+//     of four banks (no bank conflict in the update).
+//   * Steps 1 and 2: lane l takes columns (rows) l, l + 32, ...; arg-min by
+//     warp reductions on the order-preserving integer image of the float.
+//   * Step 3: lane (r, g) = (lane mod 8, lane / 8) updates rows r + 8t and
+//     16-byte column blocks g + 4u (u < U): the pivot row's U blocks stay in
+//     registers, the rows stream past with the next row's loads in flight
+//     while the current row is written.  The update is bound by the shared-
+//     memory bandwidth: 2 (m + 1)(n + 1) 4 bytes per pivot.
+//   * The next LP's A, b and c are prefetched into L2 while this LP pivots,
+//     and the tableau is built from them with 16-byte loads.
+//   * Refinement and certificate as in the register kernel (FP64 residuals,
+//     one correction with the FP32 basis inverse, KKT certificate), on
+//     operands gathered into the dead tableau region: the non-basic slacks'
+//     tableau columns and the entries of A that the FP64 products read.
+//
+// Sizes beyond the launch's limits, LPs with some b_i < 0 (Phase I) and
+// non-finite data go to the shared-memory kernel, as from the register kernel.
+
+#include "lpb_internal.cuh"
+
+namespace lpb {
+
+namespace {
+
+constexpr int kWarpMaxWarps = 8;      // LPs (warps) per CTA at most
+constexpr int kWarpMaxDim = 127;      // largest m and n: four rows (columns) per lane
+constexpr int kNoKey = 1 << 30;       // a key larger than any real key
+constexpr int kRefK = 24;             // basic structurals the on-chip refinement takes at most
+
+// One warp's region of shared memory.
+struct WarpLayout {
+  int S;          // tableau row stride in floats
+  int tab;        // bytes of the tableau region (the tableau, or more: see warp_layout)
+  int colb;       // byte offsets of the small arrays
+  int rr, dx, bas, nbv, sb, ns;
+  int bytes;      // size of the region (a multiple of 16)
+};
+
+__host__ __device__ inline int warp_stride(int max_n) {
+  int s = (max_n + 1 + 3) & ~3;
+  if ((s & 7) == 0) s += 4;          // S / 4 odd
+  return s;
+}
+
+// Arrays of one entry per row or column (float or short) hold A8 entries.
+// The tableau region holds the tableau and, after the pivots, the
+// refinement's operands; when eight regions fit the SM's shared memory with
+// room to spare, it grows towards what kRefK basic structurals need.
+__host__ __device__ inline WarpLayout warp_layout(int max_m, int max_n) {
+  WarpLayout L;
+  L.S = warp_stride(max_n);
+  const int a8 = ((max_m > max_n ? max_m : max_n) + 1 + 7) & ~7;
+  const int arrays = 20 * a8;
+  int tab = (max_m + 1) * L.S * 4;   // the tableau (16-byte rows)
+  const int want = ((max_m * (kRefK | 1) * 4 + 15) & ~15) + (kRefK + 1) * (max_m + max_n) * 8;
+  const int room = ((232448 / kWarpMaxWarps - arrays) & ~15);
+  if (want > tab && room > tab) tab = want < room ? (want + 15) & ~15 : room;
+  L.tab = tab;
+  int off = tab;
+  L.colb = off; off += 4 * a8;       // colb and rr together also serve as a[a8] doubles
+  L.rr = off;   off += 4 * a8;
+  L.dx = off;   off += 4 * a8;
+  L.bas = off;  off += 2 * a8;
+  L.nbv = off;  off += 2 * a8;
+  L.sb = off;   off += 2 * a8;
+  L.ns = off;   off += 2 * a8;
+  L.bytes = (off + 15) & ~15;
+  return L;
+}
+
+// Asynchronous 8-byte copy global -> shared; cp_async_wait_all waits for every
+// copy this thread issued.
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+
+// v[s] of the lane holding slot s = idx >> 5, from lane idx & 31 (idx is the
+// same in every lane).
+template <typename V>
+__device__ __forceinline__ V pick_slot(const V (&v)[4], int idx) {
+  const int s = idx >> 5;
+  V r = v[0];
+  if (s == 1) r = v[1];
+  if (s == 2) r = v[2];
+  if (s == 3) r = v[3];
+  return __shfl_sync(kFull, r, idx & 31);
+}
+
+// v[idx >> 5] of lane idx & 31 for a different idx in every lane.
+template <typename V>
+__device__ __forceinline__ V gather_slot(const V (&v)[4], int idx) {
+  const int src = idx & 31, s = idx >> 5;
+  const V r0 = __shfl_sync(kFull, v[0], src), r1 = __shfl_sync(kFull, v[1], src);
+  const V r2 = __shfl_sync(kFull, v[2], src), r3 = __shfl_sync(kFull, v[3], src);
+  return s == 0 ? r0 : s == 1 ? r1 : s == 2 ? r2 : r3;
+}
+
+__device__ __forceinline__ float4 upd4(float4 x, float4 p, float g) {
+  x.x = fmaf(-g, p.x, x.x);
+  x.y = fmaf(-g, p.y, x.y);
+  x.z = fmaf(-g, p.z, x.z);
+  x.w = fmaf(-g, p.w, x.w);
+  return x;
+}
+
+// Step 3's sweep: T[i, :] -= colb[i] * (pivot row) for rows i = rg + 8 t <= m,
+// on this lane's blocks cg + 4 u < nbu (pr: the pivot row's blocks).  Slots
+// whose eight rows all exist are pipelined two rows at a time; the last,
+// partial slot goes alone.  DENSE: every block but the last (u = U - 1) lies
+// below nbu in every lane.
+template <int U, bool DENSE>
+__device__ __forceinline__ void sweep_rows(float *T, int S, const float *colb, int m, int rg, int cg, int nbu,
+                                           const float4 (&pr)[U]) {
+  bool ok[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) ok[u] = (DENSE && u < U - 1) || cg + 4 * u < nbu;
+  const int full = (m + 1) >> 3;            // slots whose eight rows all exist
+  const int step = 8 * S;
+  float *row = T + rg * S + 4 * cg;
+  if (full > 0) {
+    float4 a[U], b[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (ok[u]) a[u] = ld4(row + 16 * u);
+    float ga = colb[rg], gb = 0.f;
+    int t = 0;
+    for (; t + 1 < full; t += 2) {
+      float *r1 = row + step;
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (ok[u]) b[u] = ld4(r1 + 16 * u);
+      gb = colb[rg + 8 * (t + 1)];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (ok[u]) st4(row + 16 * u, upd4(a[u], pr[u], ga));
+      float *r2 = r1 + step;
+      if (t + 2 < full) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (ok[u]) a[u] = ld4(r2 + 16 * u);
+        ga = colb[rg + 8 * (t + 2)];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (ok[u]) st4(r1 + 16 * u, upd4(b[u], pr[u], gb));
+      row = r2;
+    }
+    if (t < full) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (ok[u]) st4(row + 16 * u, upd4(a[u], pr[u], ga));
+      row += step;
+    }
+  }
+  if (rg < ((m + 1) & 7)) {                 // the partial slot
+    const float g = colb[rg + 8 * full];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (ok[u]) st4(row + 16 * u, upd4(ld4(row + 16 * u), pr[u], g));
+  }
+}
+
+// Prefetch A, b and c of an LP into L2 (a hint; nothing waits for it).
+__device__ __forceinline__ void warp_prefetch(const TableauParams &P, int m, int n, long long aoff, long long boff,
+                                              long long coff) {
+  const size_t es = P.B.dtype == LPB_DTYPE_F64 ? 8 : 4;
+  prefetch_l2(static_cast<const unsigned char *>(P.B.A) + size_t(aoff) * es, size_t(m) * size_t(n) * es);
+  prefetch_l2(static_cast<const unsigned char *>(P.B.b) + size_t(boff) * es, size_t(m) * es);
+  prefetch_l2(static_cast<const unsigned char *>(P.B.c) + size_t(coff) * es, size_t(n) * es);
+}
+
+// Rows r0..m-1 of the LP's FP64 A (Ag) converted to FP32 by truncation
+// (relative error below 2^-23; the refinement works with the exact A) into
+// the tableau by plain loads: the elements in order over the 32 lanes, eight
+// loads in flight per lane, pairs of doubles with 16-byte loads when the rows
+// start on 16-byte boundaries (16-byte aligned A, n even).  `amax` keeps the
+// largest high word of |a| (see d2f_trunc).
+__device__ __forceinline__ void build_rows_ldg(float *T, int S, const double *Ag, int r0, int m, int n, int lane,
+                                               unsigned &amax) {
+  const double *A0 = Ag + static_cast<long long>(r0) * n;
+  const int tot = (m - r0) * n;
+  if ((reinterpret_cast<uintptr_t>(A0) & 15) == 0 && (n & 1) == 0) {
+    const double2 *A2 = reinterpret_cast<const double2 *>(A0);
+    const int tot2 = tot >> 1;
+    int row = r0, col = 2 * lane;
+    while (col >= n) { col -= n; ++row; }
+    for (int k0 = lane; k0 < tot2; k0 += 32 * 8) {
+      double2 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = k0 + 32 * q;
+        if (k < tot2) v[q] = __ldg(A2 + k);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (k0 + 32 * q < tot2) {
+          float2 f;
+          f.x = d2f_trunc(v[q].x, amax);
+          f.y = d2f_trunc(v[q].y, amax);
+          *reinterpret_cast<float2 *>(T + row * S + col) = f;
+        }
+        col += 64;
+        while (col >= n) { col -= n; ++row; }
+      }
+    }
+  } else {
+    int row = r0, col = lane;
+    while (col >= n) { col -= n; ++row; }
+    for (int k0 = lane; k0 < tot; k0 += 32 * 8) {
+      double v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = k0 + 32 * q;
+        if (k < tot) v[q] = __ldg(A0 + k);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (k0 + 32 * q < tot) T[row * S + col] = d2f_trunc(v[q], amax);
+        col += 32;
+        while (col >= n) { col -= n; ++row; }
+      }
+    }
+  }
+}
+
+
+// Element i of the LP's FP64 b or c rounded to FP32 and its magnitude bits;
+// non-finite or out-of-range values set `bad`.
+__device__ __forceinline__ float vec_in(const void *v, long long i, int &bad, unsigned long long &mag) {
+  const double d = __ldg(static_cast<const double *>(v) + i);
+  mag = static_cast<unsigned long long>(__double_as_longlong(d)) & 0x7fffffffffffffffull;
+  return d2f_tile(d, bad);
+}
+
+template <int U>
+__global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauParams P, WarpLayout L) {
+  extern __shared__ __align__(16) unsigned char warp_smem[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned char *base = warp_smem + size_t(wid) * size_t(L.bytes);
+  float *T = reinterpret_cast<float *>(base);
+  float *colb = reinterpret_cast<float *>(base + L.colb);    // pivot-column multipliers; rho
+  float *rrs = reinterpret_cast<float *>(base + L.rr);       // FP32 residuals; dy by slack
+  float *dxs = reinterpret_cast<float *>(base + L.dx);       // structural corrections by row
+  double *xs = reinterpret_cast<double *>(base + L.colb);    // x of basic slacks by slack (over colb, rr)
+  short *bas = reinterpret_cast<short *>(base + L.bas);      // basic variable of each row
+  short *nbv = reinterpret_cast<short *>(base + L.nbv);      // non-basic variable of each column
+  short *sbl = reinterpret_cast<short *>(base + L.sb);       // rows of the basic structurals
+  short *nsl = reinterpret_cast<short *>(base + L.ns);       // columns of the non-basic slacks
+  const int S = L.S;
+  const int rg = lane & 7, cg = lane >> 3;
+  const int nitems = P.in.count ? min(*P.in.count, P.list_cap) : P.B.count;
+  const float eps_p = float(P.eps_p), eps_d = float(P.eps_d);
+  constexpr unsigned long long kInf = 0x7ff0000000000000ull;
+
+  if (blockDim.x > kWarpMaxWarps * 32 || (blockDim.x & 31) || P.B.dtype != LPB_DTYPE_F64) {
+    if (threadIdx.x == 0) atomicOr(P.err, ERR_BAD_LAUNCH);
+    return;
+  }
+  auto fits_lp = [&](int m, int n) {
+    return m >= 1 && n >= 1 && m <= P.lim_m && n <= P.lim_n && m <= P.B.max_m && n <= P.B.max_n &&
+           m <= kWarpMaxDim && n <= kWarpMaxDim && n + 1 <= 16 * U;
+  };
+  auto read_desc = [&](int it, int &lp_, int &m_, int &n_, long long &a_, long long &b_, long long &c_) {
+    lp_ = P.in.items ? __ldg(P.in.items + it) : it;
+    m_ = __ldg(P.B.m + lp_);
+    n_ = __ldg(P.B.n + lp_);
+    a_ = __ldg(P.B.a_off + lp_);
+    b_ = __ldg(P.B.b_off + lp_);
+    c_ = __ldg(P.B.c_off + lp_);
+  };
+
+  // Work items are claimed one LP ahead: the claim is issued when an LP
+  // starts, the claimed LP's descriptor is read while this LP's tableau is
+  // built, and its data is prefetched into L2 before this LP's pivots.
+  int item = 0;
+  if (lane == 0) item = atomicAdd(P.queue, 1);
+  item = __shfl_sync(kFull, item, 0);
+  int lp = 0, m = 0, n = 0;
+  long long aoff = 0, boff = 0, coff = 0;
+  if (item < nitems) read_desc(item, lp, m, n, aoff, boff, coff);
+  while (item < nitems) {
+    int nitem = 0;
+    if (lane == 0) nitem = atomicAdd(P.queue, 1);
+    // ---- b and c: checks (their FP32 values wait in registers, rows and
+    // columns lane + 32 s, while A is built) ----
+    const bool fits = fits_lp(m, n);
+    int bad = !fits;
+    unsigned long long bm = 0ull, cm = 0ull;
+    float bf[4], cf[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int i = lane + 32 * s;
+      bf[s] = 0.f;
+      cf[s] = 0.f;
+      if (fits && i < m) {
+        unsigned long long a;
+        bf[s] = vec_in(P.B.b, boff + i, bad, a);
+        bad |= int(__float_as_uint(bf[s]) > 0x80000000u);     // b_i < 0 (Phase I)
+        bm = a > bm ? a : bm;
+      }
+      if (fits && i < n) {
+        unsigned long long a;
+        cf[s] = vec_in(P.B.c, coff + i, bad, a);
+        cm = a > cm ? a : cm;
+      }
+    }
+    nitem = __shfl_sync(kFull, nitem, 0);
+    int nlp = 0, nm = 0, nn = 0;
+    long long na = 0, nb = 0, nc = 0;
+    if (nitem < nitems) read_desc(nitem, nlp, nm, nn, na, nb, nc);
+    if (fits) {
+      unsigned amax = 0u;
+      build_rows_ldg(T, S, static_cast<const double *>(P.B.A) + aoff, 0, m, n, lane, amax);
+      bad |= int(amax >= (1151u << 20));     // |a| >= 2^128, Inf or NaN
+      // The right-hand side column, the objective row (-c, and 0 on the
+      // right-hand side) and the zero columns n+1 .. 4 ceil((n+1)/4) - 1 that
+      // the update sweeps.
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = lane + 32 * s;
+        if (i < m) {
+          T[i * S + n] = bf[s];
+          bas[i] = short(n + i);
+        }
+        if (i < n) {
+          T[m * S + i] = -cf[s];
+          nbv[i] = short(i);
+        }
+      }
+      if (lane == 0) T[m * S + n] = 0.f;
+      const int padw = 4 * ((n + 4) >> 2) - (n + 1);
+      if (padw > 0)
+        for (int k = lane; k < (m + 1) * padw; k += 32) {
+          const int i = k / padw;
+          T[i * S + n + 1 + (k - i * padw)] = 0.f;
+        }
+    }
+    bad = __any_sync(kFull, bad);
+    if (lane == 0 && nitem < nitems && !P.shared && fits_lp(nm, nn)) warp_prefetch(P, nm, nn, na, nb, nc);
+    if (bad) {             // the shared-memory kernel handles it (Phase I, sizes, bad data)
+      if (lane == 0) {
+        P.R.status[lp] = STATUS_PENDING;
+        list_push(P.defer_items, P.defer_count, P.list_cap, lp, P.err);
+      }
+      item = nitem; lp = nlp; m = nm; n = nn; aoff = na; boff = nb; coff = nc;
+      __syncwarp();
+      continue;
+    }
+    bm = warp_max_u64(bm <= kInf ? bm : 0ull);      // NaN magnitudes take no part
+    cm = warp_max_u64(cm < kInf ? cm : 0ull);
+    __syncwarp();
+
+    // ---- Steps 1-3 ----
+    const int max_iter = P.max_iter > 0 ? P.max_iter : 50 * (m + n);
+    const int nbu = (n + 4) >> 2;              // 16-byte blocks holding columns 0..n
+    int iters = 0, status = LPB_OPTIMAL, degenerate_run = 0;
+    bool bland = false;
+    for (;;) {
+      // Step 1: column j = lane + 32 s of the objective row.  Candidates are
+      // compared on the order-preserving integer image of their value (the
+      // random rule's keys are bit patterns that may lie beyond +inf); no
+      // candidate is the largest image.
+      // The loads that do not depend on the entering column go first: the
+      // objective row and the column variables for Step 1, the right-hand
+      // side and the row variables for Step 2.
+      float rj4[4], rh4[4];
+      int nv4[4], bv4[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int j = lane + 32 * s;
+        rj4[s] = j < n ? T[m * S + j] : 0.f;
+        nv4[s] = j < n ? int(nbv[j]) : 0;
+        rh4[s] = j < m ? T[j * S + n] : 0.f;
+        bv4[s] = j < m ? int(bas[j]) : 0;
+      }
+      unsigned co = 0xffffffffu;
+      int ck = kNoKey;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int j = lane + 32 * s;
+        if (j < n) {
+          const float rj = rj4[s];
+          if (rj < -eps_d) {
+            const int v = nv4[s];
+            // The random rule ranks by the upper 31 bits of the variable's key,
+            // stored as the bits of a non-negative float.
+            const float val = bland ? 0.f
+                            : P.rule == LPB_PIVOT_RPC ? __uint_as_float(rpc_key(P.seed, P.lp_base + lp, iters, v) >> 1)
+                                                      : rj;
+            const unsigned o = f2ord(val);
+            const int key = (v << kIdxBits) | j;
+            if (o < co || (o == co && key < ck)) { co = o; ck = key; }
+          }
+        }
+      }
+      float cv = ord2f(co);
+      warp_argmin_f32(cv, ck);
+      if (ck == kNoKey) { status = LPB_OPTIMAL; break; }
+      const int e = ck & kIdxMask;
+      // Step 2: the min-ratio test over rows i = lane + 32 s (column e and the
+      // right-hand side); a[] keeps column e, with the objective row's entry.
+      float tv = __int_as_float(0x7f800000);
+      int tk = kNoKey;
+      float a[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = lane + 32 * s;
+        a[s] = i <= m ? T[i * S + e] : 0.f;
+        if (i < m && a[s] > eps_p) keep_better(tv, tk, rh4[s] * rcp_approx(a[s]), (bv4[s] << kIdxBits) | i);
+      }
+      warp_argmin_f32(tv, tk);
+      if (tk == kNoKey) { status = LPB_UNBOUNDED; break; }
+      if (iters >= max_iter) { status = LPB_ITER_LIMIT; break; }
+      const int l = tk & kIdxMask, leave_var = tk >> kIdxBits;
+      const float rp = __frcp_rn(pick_slot(a, l));
+      // Multipliers t_ie / p of every row but the pivot row (0: left alone by
+      // the sweep, then scaled).
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = lane + 32 * s;
+        a[s] = i == l ? 0.f : a[s] * rp;
+        if (i <= m) colb[i] = a[s];
+      }
+      float4 pr[U];
+      {
+        const float *rowl = T + l * S + 4 * cg;
+#pragma unroll
+        for (int u = 0; u < U; ++u) pr[u] = cg + 4 * u < nbu ? ld4(rowl + 16 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      __syncwarp();
+      // Step 3: rows rg + 8 t stream through two at a time; a row's blocks and
+      // multiplier are loaded before the row before it is written.
+      if (nbu >= 4 * U - 4) sweep_rows<U, true>(T, S, colb, m, rg, cg, nbu, pr);
+      else sweep_rows<U, false>(T, S, colb, m, rg, cg, nbu, pr);
+      __syncwarp();
+      // The pivot row scaled by 1/p from the copy in registers (one lane per
+      // column group) with 1/p at column e; column e becomes -t_ie / p.
+      if (rg == 0) {
+        float *rowl = T + l * S + 4 * cg;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int c0 = 4 * (cg + 4 * u);
+          if (c0 < 4 * nbu) {
+            float4 v = pr[u];
+            v.x = c0 == e ? rp : v.x * rp;
+            v.y = c0 + 1 == e ? rp : v.y * rp;
+            v.z = c0 + 2 == e ? rp : v.z * rp;
+            v.w = c0 + 3 == e ? rp : v.w * rp;
+            st4(rowl + 16 * u, v);
+          }
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = lane + 32 * s;
+        if (i <= m && i != l) T[i * S + e] = -a[s];
+      }
+      if (lane == 0) {
+        bas[l] = short(ck >> kIdxBits);
+        nbv[e] = short(leave_var);
+      }
+      __syncwarp();
+      ++iters;
+      if (tv <= eps_p) {
+        if (++degenerate_run >= m + n) bland = true;
+      } else {
+        degenerate_run = 0;
+        bland = false;
+      }
+    }
+
+    const int64_t yoff = P.R.y_off ? P.R.y_off[lp] : boff;    // outputs packed like b, or at y_off
+    int32_t *bp = P.bbuf ? P.bbuf + (P.bpacked ? yoff : int64_t(lp) * P.B.max_m) : nullptr;
+    if (bp)
+      for (int i = lane; i < m; i += 32) bp[i] = bas[i];
+    if (status != LPB_OPTIMAL || P.mode != MODE_FP32_REFINE) {
+      if (status == LPB_OPTIMAL) {           // plain FP32: results straight from the tableau
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int j = lane + 32 * s, i = lane + 32 * s;
+          if (j < n) {
+            const int v = nbv[j];
+            if (v < n) P.R.x[coff + v] = 0.0;
+            else if (P.R.y) P.R.y[yoff + (v - n)] = f2d_exact(T[m * S + j]);
+          }
+          if (i < m) {
+            const int v = bas[i];
+            if (v < n) P.R.x[coff + v] = f2d_exact(T[i * S + n]);
+            else if (P.R.y) P.R.y[yoff + (v - n)] = 0.0;
+          }
+        }
+        if (lane == 0) {
+          P.R.status[lp] = LPB_OPTIMAL;
+          P.R.obj[lp] = f2d_exact(T[m * S + n]);
+          if (P.R.iters) P.R.iters[lp] = iters;
+        }
+      } else if (P.mode == MODE_FP32_REFINE) {   // unbounded / iteration cap: confirm in FP64
+        if (lane == 0) {
+          P.R.status[lp] = STATUS_PENDING;
+          if (P.R.iters) P.R.iters[lp] = iters;
+          list_push(P.resolve_items, P.resolve_count, P.list_cap, lp, P.err);
+        }
+      } else {                                   // plain FP32: final as found
+        for (int j = lane; j < n; j += 32) P.R.x[coff + j] = 0.0;
+        if (P.R.y)
+          for (int i = lane; i < m; i += 32) P.R.y[yoff + i] = 0.0;
+        if (lane == 0) {
+          P.R.status[lp] = status;
+          if (P.R.iters) P.R.iters[lp] = iters;
+          P.R.obj[lp] = status == LPB_UNBOUNDED ? INFINITY : NAN;
+        }
+      }
+      item = nitem; lp = nlp; m = nm; n = nn; aoff = na; boff = nb; coff = nc;
+      __syncwarp();
+      continue;
+    }
+
+    // ---- FP64 refinement and certificate, A, b and c read from global memory ----
+    // Lists by ballot: sbl[q] is the row of the q-th basic structural, nsl[p]
+    // the column of the p-th non-basic slack (as many as basic structurals).
+    int k = 0, kn = 0;
+    for (int i0 = 0; i0 < m; i0 += 32) {
+      const int i = i0 + lane;
+      const bool in = i < m && bas[i] < n;
+      const unsigned mk = __ballot_sync(kFull, in);
+      if (in) sbl[k + __popc(mk & ((1u << lane) - 1u))] = short(i);
+      k += __popc(mk);
+    }
+    for (int j0 = 0; j0 < n; j0 += 32) {
+      const int j = j0 + lane;
+      const bool in = j < n && nbv[j] >= n;
+      const unsigned mk = __ballot_sync(kFull, in);
+      if (in) nsl[kn + __popc(mk & ((1u << lane) - 1u))] = short(j);
+      kn += __popc(mk);
+    }
+    __syncwarp();
+    // Row slot s of this lane: row lane + 32 s, its basic variable bv[s] (-1
+    // past m) and x_B; p-slot s: the non-basic slack p = lane + 32 s, its row
+    // kp[s] of A and its y.
+    int bv[4], kp[4];
+    double xb[4], yq[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int i = lane + 32 * s, p = lane + 32 * s;
+      bv[s] = i < m ? int(bas[i]) : -1;
+      xb[s] = i < m ? f2d_exact(T[i * S + n]) : 0.0;
+      const int c = p < kn ? int(nsl[p]) : 0;
+      kp[s] = p < kn ? int(nbv[c]) - n : 0;
+      yq[s] = p < kn ? f2d_exact(T[m * S + c]) : 0.0;
+    }
+    const double tol = P.feas_tol;
+    const double tp = tol * (1.0 + __longlong_as_double(static_cast<long long>(bm)));
+    const double td = tol * (1.0 + __longlong_as_double(static_cast<long long>(cm)));
+    constexpr float kDeltaErr = 1.f / 32768.f;
+    // The refinement's operands on chip: the tableau is dead after the pivots
+    // but for the non-basic slacks' columns, which move to the start of its
+    // region (compacted, odd stride), and the entries of A that the products
+    // read follow them: A's basic columns (k x m, column-major) and the
+    // non-basic slacks' rows (k x n), gathered by asynchronous copies in one
+    // round trip, and b and c after them.  An LP with more than kRefK basic
+    // structurals, or whose operands do not fit, goes to the FP64 re-solve
+    // instead.
+    const int ks = kn | 1;
+    const int off_ac = (m * ks * 4 + 15) & ~15;
+    const int off_ar = off_ac + k * m * 8;
+    const int off_bc = off_ar + kn * n * 8;
+    if (kn > kRefK || off_bc + (m + n) * 8 > L.tab) {
+      if (lane == 0) {
+        P.R.status[lp] = STATUS_PENDING;
+        if (P.R.iters) P.R.iters[lp] = iters;
+        list_push(P.resolve_items, P.resolve_count, P.list_cap, lp, P.err);
+      }
+      item = nitem; lp = nlp; m = nm; n = nn; aoff = na; boff = nb; coff = nc;
+      __syncwarp();
+      continue;
+    }
+    float *tcomp = T;                                                    // [m][ks]
+    double *ac = reinterpret_cast<double *>(base + off_ac);              // [k][m]
+    double *ar = reinterpret_cast<double *>(base + off_ar);              // [kn][n]
+    double *bsm = reinterpret_cast<double *>(base + off_bc);             // b [m], then c [n]
+    double *csm = bsm + m;
+    // Compaction 32 rows at a time: compacted rows below 32 (c + 1) end before
+    // tableau row 32 (c + 1) starts (ks < S), so no row is overwritten unread.
+    for (int c0 = 0; c0 < m; c0 += 32) {
+      const int i = c0 + lane;
+      float tc[kRefK];
+#pragma unroll
+      for (int p = 0; p < kRefK; ++p) tc[p] = (p < kn && i < m) ? T[i * S + nsl[p]] : 0.f;
+      __syncwarp();
+#pragma unroll
+      for (int p = 0; p < kRefK; ++p)
+        if (p < kn && i < m) tcomp[i * ks + p] = tc[p];
+      __syncwarp();
+    }
+    {
+      const double *Ad = static_cast<const double *>(P.B.A) + aoff;
+      for (int q = 0; q < k; ++q) {
+        const int jq = bas[sbl[q]];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int i = lane + 32 * s;
+          if (i < m) cp_async8(ac + q * m + i, Ad + static_cast<long long>(i) * n + jq);
+        }
+      }
+      for (int p = 0; p < kn; ++p) {
+        const int r = nbv[nsl[p]] - n;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int j = lane + 32 * s;
+          if (j < n) cp_async8(ar + p * n + j, Ad + static_cast<long long>(r) * n + j);
+        }
+      }
+    }
+    // b and c follow, in the same round trip.
+    {
+      const double *bg = static_cast<const double *>(P.B.b) + boff;
+      const double *cg64 = static_cast<const double *>(P.B.c) + coff;
+      for (int i = lane; i < m; i += 32) cp_async8(bsm + i, bg + i);
+      for (int j = lane; j < n; j += 32) cp_async8(csm + j, cg64 + j);
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    // A[i, j_q] of the q-th basic structural and A[k_p, j] of the p-th non-basic
+    // slack's row, as FP32 from the high word (see hi2f).
+    auto a_col_f = [&](int q, int i) -> float { return hi2f(reinterpret_cast<const unsigned *>(ac + q * m + i)[1]); };
+    auto a_row_f = [&](int p, int j) -> float { return hi2f(reinterpret_cast<const unsigned *>(ar + p * n + j)[1]); };
+    int fail = 0;
+    double cx = 0.0;
+    for (int round = 0;; ++round) {
+      // Row residuals in FP64: sax_i = b_i - sum_q A[i, j_q] x_q over the basic
+      // structurals, and r_i = sax_i minus x of slack i when it is basic.
+      double sax[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 2
+      for (int q = 0; q < k; ++q) {
+        const double xq = pick_slot(xb, int(sbl[q]));
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int i = lane + 32 * s;
+          if (i < m) sax[s] = fma(ac[q * m + i], xq, sax[s]);
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = lane + 32 * s;
+        if (i < m) {
+          sax[s] = bsm[i] - sax[s];
+          xs[i] = 0.0;
+        }
+      }
+      __syncwarp();
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        if (bv[s] >= n) xs[bv[s] - n] = xb[s];
+      __syncwarp();
+      double rr[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = lane + 32 * s;
+        rr[s] = i < m ? sax[s] - xs[i] : 0.0;
+      }
+      __syncwarp();                           // xs (over colb and rr) is rewritten below
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int i = lane + 32 * s;
+        if (i < m) rrs[i] = d2f_rn(rr[s]);
+      }
+      // Reduced costs in FP64, columns j = lane + 32 s: d_j = sum_p A[k_p, j] y_p - c_j.
+      double dj[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 2
+      for (int p = 0; p < kn; ++p) {
+        const double yv = pick_slot(yq, p);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int j = lane + 32 * s;
+          if (j < n) dj[s] = fma(ar[p * n + j], yv, dj[s]);
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int j = lane + 32 * s;
+        if (j < n) {
+          dj[s] -= csm[j];
+          dxs[j] = d2f_rn(neg_bits(dj[s]));   // -d_j by column, for rho below
+        }
+      }
+      __syncwarp();
+      // rho_t = -d of the basic structural of row t (0 for a basic slack).
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int t = lane + 32 * s;
+        if (t < m) colb[t] = unsigned(bv[s]) < unsigned(n) ? dxs[bv[s]] : 0.f;
+      }
+      // Corrections with the FP32 basis inverse, whose column for slack k is the
+      // tableau column of k when k is non-basic, else a unit vector:
+      //   dx_t = sum_p T[t, c_p] r_{k_p} (+ r of the slack itself in a basic slack's row).
+      float dxv[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+      for (int p = 0; p < kn; ++p) {
+        const float coef = rrs[pick_slot(kp, p)];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int t = lane + 32 * s;
+          if (t < m) dxv[s] = fmaf(tcomp[t * ks + p], coef, dxv[s]);
+        }
+      }
+      double rsl[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) rsl[s] = gather_slot(rr, bv[s] >= n ? bv[s] - n : 0);
+      __syncwarp();                           // colb is complete; rrs and dxs are rewritten below
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int t = lane + 32 * s;
+        if (t < m) {
+          const double d = f2d_exact(dxv[s]);
+          xb[s] += bv[s] >= n ? d + rsl[s] : d;
+          dxs[t] = bv[s] < n ? dxv[s] : 0.f;   // the structural part of the correction
+        }
+      }
+      // dy_p = sum_t T[t, c_p] rho_t for the non-basic slacks p = lane + 32 s.
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        if (32 * s >= kn) break;
+        const int p = lane + 32 * s;
+        if (p < kn) {
+          float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+          int t = 0;
+          for (; t + 3 < m; t += 4) {
+            a0 = fmaf(tcomp[t * ks + p], colb[t], a0);
+            a1 = fmaf(tcomp[(t + 1) * ks + p], colb[t + 1], a1);
+            a2 = fmaf(tcomp[(t + 2) * ks + p], colb[t + 2], a2);
+            a3 = fmaf(tcomp[(t + 3) * ks + p], colb[t + 3], a3);
+          }
+          for (; t < m; ++t) a0 = fmaf(tcomp[t * ks + p], colb[t], a0);
+          const float dy = (a0 + a1) + (a2 + a3);
+          yq[s] += f2d_exact(dy);
+          rrs[kp[s]] = dy;                    // dy by slack, for the certificate
+        }
+      }
+      __syncwarp();
+      // KKT certificate of the pair that is written out (x: the structural part
+      // of x_B; y: the slack duals): x >= 0, A x <= b, y >= 0, A^T y >= c and
+      // c^T x = b^T y, each to tol scaled by the data.  b - A x and A^T y - c at
+      // the corrected point are the FP64 values above plus FP32 products with
+      // the corrections, whose rounding (and the 2^-20 truncation of A) is
+      // bounded by 2^-15 times the sum of the products' magnitudes.
+      fail = 0;
+      double cxp = 0.0, byp = 0.0;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        if (unsigned(bv[s]) < unsigned(n)) {
+          fail |= !dge(xb[s], neg_bits(tp));
+          cxp = fma(csm[bv[s]], xb[s], cxp);
+        }
+        if (lane + 32 * s < kn) {
+          fail |= !dge(yq[s], neg_bits(td));
+          byp = fma(bsm[kp[s]], yq[s], byp);
+        }
+      }
+      {
+        float dl[4] = {0.f, 0.f, 0.f, 0.f}, mg[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+        for (int q = 0; q < k; ++q) {          // slack b_i - A_i x of every row
+          const float d = dxs[sbl[q]];
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const int i = lane + 32 * s;
+            if (i < m) {
+              const float a = a_col_f(q, i);
+              dl[s] = fmaf(a, d, dl[s]);
+              mg[s] = fmaf(fabsf(a), fabsf(d), mg[s]);
+            }
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          if (lane + 32 * s < m) fail |= !dge(sax[s] - f2d_exact(dl[s] + kDeltaErr * mg[s]), neg_bits(tp));
+      }
+      {
+        float dl[4] = {0.f, 0.f, 0.f, 0.f}, mg[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+        for (int p = 0; p < kn; ++p) {         // reduced cost A_j^T y - c_j of every column
+          const int r = pick_slot(kp, p);
+          const float d = rrs[r];
+#pragma unroll
+          for (int s = 0; s < 4; ++s) {
+            const int j = lane + 32 * s;
+            if (j < n) {
+              const float a = a_row_f(p, j);
+              dl[s] = fmaf(a, d, dl[s]);
+              mg[s] = fmaf(fabsf(a), fabsf(d), mg[s]);
+            }
+          }
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          if (lane + 32 * s < n) fail |= !dge(dj[s] + f2d_exact(dl[s] - kDeltaErr * mg[s]), neg_bits(td));
+      }
+      cx = warp_sum(cxp);
+      const double by = warp_sum(byp);
+      fail |= !(fabs(cx - by) <= tol * (1.0 + fabs(cx)));
+      fail = __any_sync(kFull, fail);
+      if (!fail || round == 2) break;
+      __syncwarp();          // the scratch arrays are rewritten by the next round
+    }
+    if (!fail) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int j = lane + 32 * s;
+        if (j < n && nbv[j] < n) P.R.x[coff + nbv[j]] = 0.0;
+        if (unsigned(bv[s]) < unsigned(n)) P.R.x[coff + bv[s]] = xb[s];
+        if (P.R.y) {
+          if (bv[s] >= n) P.R.y[yoff + (bv[s] - n)] = 0.0;
+          if (lane + 32 * s < kn) P.R.y[yoff + kp[s]] = yq[s];
+        }
+      }
+    }
+    if (lane == 0) {
+      if (!fail) {
+        P.R.status[lp] = LPB_OPTIMAL;
+        P.R.obj[lp] = cx;
+      } else {
+        P.R.status[lp] = STATUS_PENDING;
+        list_push(P.resolve_items, P.resolve_count, P.list_cap, lp, P.err);
+      }
+      if (P.R.iters) P.R.iters[lp] = iters;
+    }
+    item = nitem; lp = nlp; m = nm; n = nn; aoff = na; boff = nb; coff = nc;
+    __syncwarp();
+  }
+}
+
+template <int U>
+const void *warp_fn() {
+  return reinterpret_cast<const void *>(&warp_kernel<U>);
+}
+
+// Column blocks per lane for LPs up to max_n columns (n + 1 <= 16 U).
+int warp_u(int max_n) {
+  int u = ((max_n + 1 + 3) / 4 + 3) / 4;
+  return u < 2 ? 2 : u;
+}
+
+const void *warp_kernel_for(int u) {
+  switch (u) {
+    case 2: return warp_fn<2>();
+    case 3: return warp_fn<3>();
+    case 4: return warp_fn<4>();
+    case 5: return warp_fn<5>();
+    case 6: return warp_fn<6>();
+    case 7: return warp_fn<7>();
+    case 8: return warp_fn<8>();
+    default: return nullptr;
+  }
+}
+
+}  // namespace
+
+bool warp_fits(int max_m, int max_n) {
+  return max_m >= 1 && max_n >= 1 && max_m <= kWarpMaxDim && max_n <= kWarpMaxDim;
+}
+
+// Warps (LPs) per CTA and shared memory of the warp kernel for LPs up to
+// max_m x max_n: as many warps as the SM's shared memory holds regions, at most
+// eight; CTAs per SM from the occupancy calculator.
+cudaError_t warp_occupancy(int max_m, int max_n, int *ctas, int *threads, size_t *smem) {
+  *ctas = 0;
+  if (!warp_fits(max_m, max_n)) return cudaErrorInvalidValue;
+  const WarpLayout L = warp_layout(max_m, max_n);
+  int nw = int(size_t(232448) / size_t(L.bytes));
+  if (nw > kWarpMaxWarps) nw = kWarpMaxWarps;
+  if (nw < 1) return cudaSuccess;
+  *threads = 32 * nw;
+  *smem = size_t(nw) * size_t(L.bytes);
+  const void *fn = warp_kernel_for(warp_u(max_n));
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(*smem));
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fn, *threads, *smem);
+}
+
+cudaError_t launch_warp(const TableauParams &p, int grid, int threads, size_t smem, cudaStream_t s) {
+  if (!warp_fits(p.lim_m, p.lim_n)) return cudaErrorInvalidValue;
+  const WarpLayout L = warp_layout(p.lim_m, p.lim_n);
+  if (size_t(threads / 32) * size_t(L.bytes) > smem) return cudaErrorInvalidValue;
+  const void *fn = warp_kernel_for(warp_u(p.lim_n));
+  if (!fn) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  WarpLayout lay = L;
+  void *args[] = {const_cast<TableauParams *>(&p), &lay};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(threads), args, smem, s);
+}
+
+}  // namespace lpb

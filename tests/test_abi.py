@@ -86,7 +86,7 @@ def test_enum_values_match_header(tmp_path):
     names = ["OPTIMAL", "INFEASIBLE", "UNBOUNDED", "ITER_LIMIT", "NUMERIC", "BAD_SIZE",
              "OK", "EINVAL", "ENOMEM", "ECUDA", "EUNSUPPORTED", "EDEVICE",
              "FP64", "FP32_REFINE", "FP32", "DTYPE_F32", "DTYPE_F64",
-             "KERNEL_AUTO", "KERNEL_SMEM", "KERNEL_GMEM", "KERNEL_REG",
+             "KERNEL_AUTO", "KERNEL_SMEM", "KERNEL_GMEM", "KERNEL_REG", "KERNEL_PACK", "KERNEL_WARP",
              "PIVOT_LPC", "PIVOT_RPC", "PIVOT_STEEPEST"]
     prog = tmp_path / "enums.c"
     body = "".join(f'printf("{n} %d\\n", (int)LPB_{n});' for n in names)
