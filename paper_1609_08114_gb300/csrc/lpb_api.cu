@@ -200,21 +200,33 @@ lpb_err pack_pass(const DeviceInfo &d, const lpb_batch *b, int lanes, int mode, 
   return LPB_OK;
 }
 
-lpb_err warp_pass(const DeviceInfo &d, const lpb_batch *b, int mode, Pass *p) {
+lpb_err warp_pass(const DeviceInfo &d, const lpb_batch *b, int lim_m, int lim_n, int mode, Pass *p) {
   int occ = 0;
-  if (warp_occupancy(b->max_m, b->max_n, &occ, &p->threads, &p->smem) != cudaSuccess) return LPB_ECUDA;
+  if (warp_occupancy(lim_m, lim_n, &occ, &p->threads, &p->smem) != cudaSuccess) return LPB_ECUDA;
   if (occ < 1 || p->smem > d.smem_optin) return LPB_EUNSUPPORTED;
   p->fp64 = false;
   p->mode = mode;
   p->warp = true;
-  p->lim_m = b->max_m;
-  p->lim_n = b->max_n;
+  p->lim_m = lim_m;
+  p->lim_n = lim_n;
   // Each warp takes one LP at a time: no more CTAs than groups of LPs.
   const long long warps_per_cta = p->threads / 32;
   const long long need = (static_cast<long long>(b->count) + warps_per_cta - 1) / warps_per_cta;
   p->grid = occ * d.sms;
   if (need < p->grid) p->grid = int(need > 0 ? need : 1);
   return LPB_OK;
+}
+
+// Whether the planner gives LPs up to lim_m x lim_n the one-warp-per-LP
+// shared-memory kernel: FP32 modes with FP64 input, the largest-coefficient or
+// random rule, no kernel shape asked for, m and n from 32 (smaller LPs go
+// several per warp) to where it is measured faster than the register kernel:
+// m n <= 6600 with the FP64 refinement (up to 80 x 80), m, n <= 100 without.
+bool warp_auto(const lpb_batch *b, const lpb_options *o, int mode, int lim_m, int lim_n) {
+  if (o->kernel != LPB_KERNEL_AUTO || o->threads != 0 || o->reg_warps != 0) return false;
+  if (mode == MODE_FP64 || b->dtype != LPB_DTYPE_F64 || o->pivot_rule == LPB_PIVOT_STEEPEST) return false;
+  if (!warp_fits(lim_m, lim_n) || (lim_m < 32 && lim_n < 32)) return false;
+  return mode == MODE_FP32 ? (lim_m <= 100 && lim_n <= 100) : lim_m * lim_n <= 6600;
 }
 
 lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o, bool basis_given,
@@ -265,15 +277,23 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
   if (o->kernel == LPB_KERNEL_WARP) {
     if (!fp32 || se || b->dtype != LPB_DTYPE_F64 || !warp_fits(b->max_m, b->max_n)) return LPB_EUNSUPPORTED;
     Pass &p = pl->pass[0];
-    if ((e = warp_pass(d, b, mode, &p)) != LPB_OK) return e;
+    if ((e = warp_pass(d, b, b->max_m, b->max_n, mode, &p)) != LPB_OK) return e;
     p.list = LIST_ALL;
     np = 1;
     og.kernel = LPB_KERNEL_AUTO;
     og.threads = 0;
   }
+  // ... and the planner's choice for batches of one size where it is faster.
+  if (np == 0 && uniform && warp_auto(b, o, mode, b->max_m, b->max_n)) {
+    Pass &p = pl->pass[0];
+    if ((e = warp_pass(d, b, b->max_m, b->max_n, mode, &p)) != LPB_OK) return e;
+    p.list = LIST_ALL;
+    np = 1;
+  }
   if (np == 0 && fp32 && o->kernel == LPB_KERNEL_AUTO && !uniform) {
     // Size classes: the register-tableau templates with `want_w` warps in
-    // increasing size, then the shared-memory / L2-slot kernel for the rest.
+    // increasing size (a class the one-warp-per-LP kernel is faster for takes
+    // that kernel), then the shared-memory / L2-slot kernel for the rest.
     Pass regp[kMaxClasses];
     int nreg = 0;
     bool covered = false;
@@ -296,7 +316,12 @@ lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o,
       const int lm = mm < b->max_m ? mm : b->max_m, ln = nn < b->max_n ? nn : b->max_n;
       if (nreg > 0 && lm <= pl->cls_m[nreg - 1] && ln <= pl->cls_n[nreg - 1]) continue;
       Pass p;
-      if (reg_pass(d, b, order[a], lm, ln, mode, o->pivot_rule, &p) != LPB_OK) continue;
+      // A class the one-warp-per-LP kernel is faster for takes it instead.
+      if (warp_auto(b, o, mode, lm, ln)) {
+        if (warp_pass(d, b, lm, ln, mode, &p) != LPB_OK) continue;
+      } else if (reg_pass(d, b, order[a], lm, ln, mode, o->pivot_rule, &p) != LPB_OK) {
+        continue;
+      }
       p.list = LIST_CLASS;
       p.cls = nreg;
       pl->cls_m[nreg] = lm;
