@@ -7,7 +7,7 @@ refinement and KKT certificate, FP64 re-solve of failures, outputs.  Prints one 
 
 Secondary legs (skip with ``--no-legs``) time the other workloads once each with CUDA
 events: 1,000 x m=n=16; the m=n sweep (5, 7, 12, 15 and 28 at 100,000 LPs: several tiny
-LPs per warp up to 15); the two Step 1 rules (most negative reduced cost vs a random
+LPs per warp up to 15; 50 and 64: one warp per LP, the tableau in shared memory); the two Step 1 rules (most negative reduced cost vs a random
 eligible column) and steepest edge on 50,000 x m=n=100; one m=n=100 polytope in 50,000
 directions (shared constraints); 10,000 x m=n=100 with bounds l <= x <= u; 10,000 x m=n=200
 two-phase (largest coefficient and steepest edge); hyperbox support functions (4,000,000 x 5
@@ -490,7 +490,7 @@ def secondary_legs(solver, dev):
     solve_leg("type1_1000x16", LPBatch.from_packed(sb.m, sb.n, sb.A, sb.b, sb.c, device=dev))
     # the m=n sweep at 10,000 LPs (2,000 at 300)
     for mn, cnt in ((5, 10_000), (5, 100_000), (7, 100_000), (12, 100_000), (15, 100_000), (28, 10_000),
-                    (28, 100_000), (50, 10_000), (200, 10_000), (300, 2_000)):
+                    (28, 100_000), (50, 10_000), (64, 50_000), (200, 10_000), (300, 2_000)):
         solve_leg(f"type1_{cnt}x{mn}", _type1_device(cnt, mn, mn, dev, seed=mn), reps=3)
         torch.cuda.empty_cache()
     # the paper's comparison of Step 1 rules (Section 5): the most negative reduced cost

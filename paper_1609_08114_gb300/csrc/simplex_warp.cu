@@ -104,15 +104,6 @@ __device__ __forceinline__ V pick_slot(const V (&v)[4], int idx) {
   return __shfl_sync(kFull, r, idx & 31);
 }
 
-// v[idx >> 5] of lane idx & 31 for a different idx in every lane.
-template <typename V>
-__device__ __forceinline__ V gather_slot(const V (&v)[4], int idx) {
-  const int src = idx & 31, s = idx >> 5;
-  const V r0 = __shfl_sync(kFull, v[0], src), r1 = __shfl_sync(kFull, v[1], src);
-  const V r2 = __shfl_sync(kFull, v[2], src), r3 = __shfl_sync(kFull, v[3], src);
-  return s == 0 ? r0 : s == 1 ? r1 : s == 2 ? r2 : r3;
-}
-
 __device__ __forceinline__ float4 upd4(float4 x, float4 p, float g) {
   x.x = fmaf(-g, p.x, x.x);
   x.y = fmaf(-g, p.y, x.y);
@@ -124,14 +115,13 @@ __device__ __forceinline__ float4 upd4(float4 x, float4 p, float g) {
 // Step 3's sweep: T[i, :] -= colb[i] * (pivot row) for rows i = rg + 8 t <= m,
 // on this lane's blocks cg + 4 u < nbu (pr: the pivot row's blocks).  Slots
 // whose eight rows all exist are pipelined two rows at a time; the last,
-// partial slot goes alone.  DENSE: every block but the last (u = U - 1) lies
-// below nbu in every lane.
-template <int U, bool DENSE>
+// partial slot goes alone.
+template <int U>
 __device__ __forceinline__ void sweep_rows(float *T, int S, const float *colb, int m, int rg, int cg, int nbu,
                                            const float4 (&pr)[U]) {
   bool ok[U];
 #pragma unroll
-  for (int u = 0; u < U; ++u) ok[u] = (DENSE && u < U - 1) || cg + 4 * u < nbu;
+  for (int u = 0; u < U; ++u) ok[u] = cg + 4 * u < nbu;
   const int full = (m + 1) >> 3;            // slots whose eight rows all exist
   const int step = 8 * S;
   float *row = T + rg * S + 4 * cg;
@@ -448,8 +438,7 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       __syncwarp();
       // Step 3: rows rg + 8 t stream through two at a time; a row's blocks and
       // multiplier are loaded before the row before it is written.
-      if (nbu >= 4 * U - 4) sweep_rows<U, true>(T, S, colb, m, rg, cg, nbu, pr);
-      else sweep_rows<U, false>(T, S, colb, m, rg, cg, nbu, pr);
+      sweep_rows<U>(T, S, colb, m, rg, cg, nbu, pr);
       __syncwarp();
       // The pivot row scaled by 1/p from the copy in registers (one lane per
       // column group) with 1/p at column e; column e becomes -t_ie / p.
@@ -533,7 +522,7 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       continue;
     }
 
-    // ---- FP64 refinement and certificate, A, b and c read from global memory ----
+    // ---- FP64 refinement and certificate ----
     // Lists by ballot: sbl[q] is the row of the q-th basic structural, nsl[p]
     // the column of the p-th non-basic slack (as many as basic structurals).
     int k = 0, kn = 0;
@@ -552,37 +541,22 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       kn += __popc(mk);
     }
     __syncwarp();
-    // Row slot s of this lane: row lane + 32 s, its basic variable bv[s] (-1
-    // past m) and x_B; p-slot s: the non-basic slack p = lane + 32 s, its row
-    // kp[s] of A and its y.
-    int bv[4], kp[4];
-    double xb[4], yq[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int i = lane + 32 * s, p = lane + 32 * s;
-      bv[s] = i < m ? int(bas[i]) : -1;
-      xb[s] = i < m ? f2d_exact(T[i * S + n]) : 0.0;
-      const int c = p < kn ? int(nsl[p]) : 0;
-      kp[s] = p < kn ? int(nbv[c]) - n : 0;
-      yq[s] = p < kn ? f2d_exact(T[m * S + c]) : 0.0;
-    }
-    const double tol = P.feas_tol;
-    const double tp = tol * (1.0 + __longlong_as_double(static_cast<long long>(bm)));
-    const double td = tol * (1.0 + __longlong_as_double(static_cast<long long>(cm)));
-    constexpr float kDeltaErr = 1.f / 32768.f;
-    // The refinement's operands on chip: the tableau is dead after the pivots
-    // but for the non-basic slacks' columns, which move to the start of its
-    // region (compacted, odd stride), and the entries of A that the products
-    // read follow them: A's basic columns (k x m, column-major) and the
-    // non-basic slacks' rows (k x n), gathered by asynchronous copies in one
-    // round trip, and b and c after them.  An LP with more than kRefK basic
-    // structurals, or whose operands do not fit, goes to the FP64 re-solve
-    // instead.
+    // The refinement's operands and state on chip: the tableau is dead after
+    // the pivots but for its right-hand side, its objective row and the
+    // non-basic slacks' columns.  The latter move to the start of the region
+    // (compacted, odd stride); the entries of A that the products read follow
+    // (A's basic columns, k x m column-major, and the non-basic slacks' rows,
+    // k x n, gathered by asynchronous copies in one round trip with b and c),
+    // then the FP64 state: x of each row's basic variable, b - A x and the
+    // residual by row, the reduced costs by column, y by non-basic slack.  An
+    // LP with more than kRefK basic structurals, or whose operands do not fit,
+    // goes to the FP64 re-solve instead.
     const int ks = kn | 1;
     const int off_ac = (m * ks * 4 + 15) & ~15;
     const int off_ar = off_ac + k * m * 8;
     const int off_bc = off_ar + kn * n * 8;
-    if (kn > kRefK || off_bc + (m + n) * 8 > L.tab) {
+    const int off_st = off_bc + (m + n) * 8;
+    if (kn > kRefK || off_st + (3 * m + n + kn) * 8 + kRefK * 4 > L.tab) {
       if (lane == 0) {
         P.R.status[lp] = STATUS_PENDING;
         if (P.R.iters) P.R.iters[lp] = iters;
@@ -592,167 +566,118 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       __syncwarp();
       continue;
     }
+    // x_B and y from the FP32 tableau, before the region is reused.
+    float xf[4], yf = 0.f;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) xf[s] = lane + 32 * s < m ? T[(lane + 32 * s) * S + n] : 0.f;
+    if (lane < kn) yf = T[m * S + nsl[lane]];
     float *tcomp = T;                                                    // [m][ks]
     double *ac = reinterpret_cast<double *>(base + off_ac);              // [k][m]
     double *ar = reinterpret_cast<double *>(base + off_ar);              // [kn][n]
     double *bsm = reinterpret_cast<double *>(base + off_bc);             // b [m], then c [n]
     double *csm = bsm + m;
-    // Compaction 32 rows at a time: compacted rows below 32 (c + 1) end before
-    // tableau row 32 (c + 1) starts (ks < S), so no row is overwritten unread.
-    for (int c0 = 0; c0 < m; c0 += 32) {
-      const int i = c0 + lane;
-      float tc[kRefK];
+    double *xrow = reinterpret_cast<double *>(base + off_st);            // x of row t's basic variable
+    double *saxs = xrow + m;                                             // b - A x by row
+    double *rrd = saxs + m;                                              // residual r by row
+    double *djs = rrd + m;                                               // reduced cost by column
+    double *yqs = djs + n;                                               // y of the p-th non-basic slack
+    float *coef = reinterpret_cast<float *>(yqs + kn);                   // r of the p-th non-basic slack
+    // Compaction four rows at a time in row order, lane p taking column p:
+    // compacted rows up to i end before tableau row i + 1 starts (ks < S), so
+    // no row is overwritten unread.
+    {
+      const int c = lane < kn ? int(nsl[lane]) : 0;
+      for (int i0 = 0; i0 < m; i0 += 4) {
+        float v[4];
 #pragma unroll
-      for (int p = 0; p < kRefK; ++p) tc[p] = (p < kn && i < m) ? T[i * S + nsl[p]] : 0.f;
-      __syncwarp();
+        for (int r = 0; r < 4; ++r) v[r] = (lane < kn && i0 + r < m) ? T[(i0 + r) * S + c] : 0.f;
+        __syncwarp();
 #pragma unroll
-      for (int p = 0; p < kRefK; ++p)
-        if (p < kn && i < m) tcomp[i * ks + p] = tc[p];
-      __syncwarp();
+        for (int r = 0; r < 4; ++r)
+          if (lane < kn && i0 + r < m) tcomp[(i0 + r) * ks + lane] = v[r];
+        __syncwarp();
+      }
     }
     {
       const double *Ad = static_cast<const double *>(P.B.A) + aoff;
       for (int q = 0; q < k; ++q) {
         const int jq = bas[sbl[q]];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const int i = lane + 32 * s;
-          if (i < m) cp_async8(ac + q * m + i, Ad + static_cast<long long>(i) * n + jq);
-        }
+        for (int i = lane; i < m; i += 32) cp_async8(ac + q * m + i, Ad + static_cast<long long>(i) * n + jq);
       }
       for (int p = 0; p < kn; ++p) {
         const int r = nbv[nsl[p]] - n;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const int j = lane + 32 * s;
-          if (j < n) cp_async8(ar + p * n + j, Ad + static_cast<long long>(r) * n + j);
-        }
+        for (int j = lane; j < n; j += 32) cp_async8(ar + p * n + j, Ad + static_cast<long long>(r) * n + j);
       }
-    }
-    // b and c follow, in the same round trip.
-    {
       const double *bg = static_cast<const double *>(P.B.b) + boff;
       const double *cg64 = static_cast<const double *>(P.B.c) + coff;
       for (int i = lane; i < m; i += 32) cp_async8(bsm + i, bg + i);
       for (int j = lane; j < n; j += 32) cp_async8(csm + j, cg64 + j);
     }
+#pragma unroll
+    for (int s = 0; s < 4; ++s)
+      if (lane + 32 * s < m) xrow[lane + 32 * s] = f2d_exact(xf[s]);
+    if (lane < kn) yqs[lane] = f2d_exact(yf);
     cp_async_wait_all();
     __syncwarp();
-    // A[i, j_q] of the q-th basic structural and A[k_p, j] of the p-th non-basic
-    // slack's row, as FP32 from the high word (see hi2f).
-    auto a_col_f = [&](int q, int i) -> float { return hi2f(reinterpret_cast<const unsigned *>(ac + q * m + i)[1]); };
-    auto a_row_f = [&](int p, int j) -> float { return hi2f(reinterpret_cast<const unsigned *>(ar + p * n + j)[1]); };
+    const double tol = P.feas_tol;
+    const double tp = tol * (1.0 + __longlong_as_double(static_cast<long long>(bm)));
+    const double td = tol * (1.0 + __longlong_as_double(static_cast<long long>(cm)));
+    constexpr float kDeltaErr = 1.f / 32768.f;
     int fail = 0;
     double cx = 0.0;
     for (int round = 0;; ++round) {
-      // Row residuals in FP64: sax_i = b_i - sum_q A[i, j_q] x_q over the basic
-      // structurals, and r_i = sax_i minus x of slack i when it is basic.
-      double sax[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 2
-      for (int q = 0; q < k; ++q) {
-        const double xq = pick_slot(xb, int(sbl[q]));
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const int i = lane + 32 * s;
-          if (i < m) sax[s] = fma(ac[q * m + i], xq, sax[s]);
-        }
-      }
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int i = lane + 32 * s;
-        if (i < m) {
-          sax[s] = bsm[i] - sax[s];
-          xs[i] = 0.0;
-        }
+      // Row residuals in FP64: b_i - sum_q A[i, j_q] x_q over the basic
+      // structurals, and r_i: that minus x of slack i when it is basic.
+      for (int i = lane; i < m; i += 32) {
+        double acc = 0.0;
+        for (int q = 0; q < k; ++q) acc = fma(ac[q * m + i], xrow[sbl[q]], acc);
+        saxs[i] = bsm[i] - acc;
+        xs[i] = 0.0;
       }
       __syncwarp();
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-        if (bv[s] >= n) xs[bv[s] - n] = xb[s];
+      for (int t = lane; t < m; t += 32)
+        if (bas[t] >= n) xs[bas[t] - n] = xrow[t];
       __syncwarp();
-      double rr[4];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int i = lane + 32 * s;
-        rr[s] = i < m ? sax[s] - xs[i] : 0.0;
-      }
+      for (int i = lane; i < m; i += 32) rrd[i] = saxs[i] - xs[i];
       __syncwarp();                           // xs (over colb and rr) is rewritten below
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int i = lane + 32 * s;
-        if (i < m) rrs[i] = d2f_rn(rr[s]);
-      }
-      // Reduced costs in FP64, columns j = lane + 32 s: d_j = sum_p A[k_p, j] y_p - c_j.
-      double dj[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll 2
-      for (int p = 0; p < kn; ++p) {
-        const double yv = pick_slot(yq, p);
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const int j = lane + 32 * s;
-          if (j < n) dj[s] = fma(ar[p * n + j], yv, dj[s]);
-        }
-      }
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int j = lane + 32 * s;
-        if (j < n) {
-          dj[s] -= csm[j];
-          dxs[j] = d2f_rn(neg_bits(dj[s]));   // -d_j by column, for rho below
-        }
+      for (int i = lane; i < m; i += 32) rrs[i] = d2f_rn(rrd[i]);
+      // Reduced costs in FP64: d_j = sum_p A[k_p, j] y_p - c_j.
+      for (int j = lane; j < n; j += 32) {
+        double acc = 0.0;
+        for (int p = 0; p < kn; ++p) acc = fma(ar[p * n + j], yqs[p], acc);
+        const double d = acc - csm[j];
+        djs[j] = d;
+        dxs[j] = d2f_rn(neg_bits(d));         // -d_j by column, for rho below
       }
       __syncwarp();
-      // rho_t = -d of the basic structural of row t (0 for a basic slack).
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int t = lane + 32 * s;
-        if (t < m) colb[t] = unsigned(bv[s]) < unsigned(n) ? dxs[bv[s]] : 0.f;
-      }
+      // rho_t = -d of the basic structural of row t (0 for a basic slack); the
+      // residuals of the non-basic slacks, by p.
+      for (int t = lane; t < m; t += 32) colb[t] = bas[t] < n ? dxs[bas[t]] : 0.f;
+      if (lane < kn) coef[lane] = rrs[nbv[nsl[lane]] - n];
+      __syncwarp();
       // Corrections with the FP32 basis inverse, whose column for slack k is the
       // tableau column of k when k is non-basic, else a unit vector:
       //   dx_t = sum_p T[t, c_p] r_{k_p} (+ r of the slack itself in a basic slack's row).
-      float dxv[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
-      for (int p = 0; p < kn; ++p) {
-        const float coef = rrs[pick_slot(kp, p)];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-          const int t = lane + 32 * s;
-          if (t < m) dxv[s] = fmaf(tcomp[t * ks + p], coef, dxv[s]);
-        }
+      for (int t = lane; t < m; t += 32) {
+        float acc = 0.f;
+        for (int p = 0; p < kn; ++p) acc = fmaf(tcomp[t * ks + p], coef[p], acc);
+        const int v = bas[t];
+        const double d = f2d_exact(acc);
+        xrow[t] += v >= n ? d + rrd[v - n] : d;
+        dxs[t] = v < n ? acc : 0.f;            // the structural part of the correction
       }
-      double rsl[4];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) rsl[s] = gather_slot(rr, bv[s] >= n ? bv[s] - n : 0);
-      __syncwarp();                           // colb is complete; rrs and dxs are rewritten below
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int t = lane + 32 * s;
-        if (t < m) {
-          const double d = f2d_exact(dxv[s]);
-          xb[s] += bv[s] >= n ? d + rsl[s] : d;
-          dxs[t] = bv[s] < n ? dxv[s] : 0.f;   // the structural part of the correction
+      // dy_p = sum_t T[t, c_p] rho_t for the non-basic slacks (kn <= 32).
+      if (lane < kn) {
+        float a0 = 0.f, a1 = 0.f;
+        int t = 0;
+        for (; t + 1 < m; t += 2) {
+          a0 = fmaf(tcomp[t * ks + lane], colb[t], a0);
+          a1 = fmaf(tcomp[(t + 1) * ks + lane], colb[t + 1], a1);
         }
-      }
-      // dy_p = sum_t T[t, c_p] rho_t for the non-basic slacks p = lane + 32 s.
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        if (32 * s >= kn) break;
-        const int p = lane + 32 * s;
-        if (p < kn) {
-          float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-          int t = 0;
-          for (; t + 3 < m; t += 4) {
-            a0 = fmaf(tcomp[t * ks + p], colb[t], a0);
-            a1 = fmaf(tcomp[(t + 1) * ks + p], colb[t + 1], a1);
-            a2 = fmaf(tcomp[(t + 2) * ks + p], colb[t + 2], a2);
-            a3 = fmaf(tcomp[(t + 3) * ks + p], colb[t + 3], a3);
-          }
-          for (; t < m; ++t) a0 = fmaf(tcomp[t * ks + p], colb[t], a0);
-          const float dy = (a0 + a1) + (a2 + a3);
-          yq[s] += f2d_exact(dy);
-          rrs[kp[s]] = dy;                    // dy by slack, for the certificate
-        }
+        if (t < m) a0 = fmaf(tcomp[t * ks + lane], colb[t], a0);
+        const float dy = a0 + a1;
+        yqs[lane] += f2d_exact(dy);
+        rrs[nbv[nsl[lane]] - n] = dy;          // dy by slack, for the certificate
       }
       __syncwarp();
       // KKT certificate of the pair that is written out (x: the structural part
@@ -763,55 +688,32 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       // bounded by 2^-15 times the sum of the products' magnitudes.
       fail = 0;
       double cxp = 0.0, byp = 0.0;
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        if (unsigned(bv[s]) < unsigned(n)) {
-          fail |= !dge(xb[s], neg_bits(tp));
-          cxp = fma(csm[bv[s]], xb[s], cxp);
+      for (int i = lane; i < m; i += 32) {      // x >= 0, and the slack b_i - A_i x of every row
+        const int v = bas[i];
+        if (v < n) {
+          fail |= !dge(xrow[i], neg_bits(tp));
+          cxp = fma(csm[v], xrow[i], cxp);
         }
-        if (lane + 32 * s < kn) {
-          fail |= !dge(yq[s], neg_bits(td));
-          byp = fma(bsm[kp[s]], yq[s], byp);
+        float dl = 0.f, mg = 0.f;
+        for (int q = 0; q < k; ++q) {
+          const float a = hi2f(reinterpret_cast<const unsigned *>(ac + q * m + i)[1]), d = dxs[sbl[q]];
+          dl = fmaf(a, d, dl);
+          mg = fmaf(fabsf(a), fabsf(d), mg);
         }
+        fail |= !dge(saxs[i] - f2d_exact(dl + kDeltaErr * mg), neg_bits(tp));
       }
-      {
-        float dl[4] = {0.f, 0.f, 0.f, 0.f}, mg[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
-        for (int q = 0; q < k; ++q) {          // slack b_i - A_i x of every row
-          const float d = dxs[sbl[q]];
-#pragma unroll
-          for (int s = 0; s < 4; ++s) {
-            const int i = lane + 32 * s;
-            if (i < m) {
-              const float a = a_col_f(q, i);
-              dl[s] = fmaf(a, d, dl[s]);
-              mg[s] = fmaf(fabsf(a), fabsf(d), mg[s]);
-            }
-          }
-        }
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-          if (lane + 32 * s < m) fail |= !dge(sax[s] - f2d_exact(dl[s] + kDeltaErr * mg[s]), neg_bits(tp));
+      if (lane < kn) {                          // y >= 0
+        fail |= !dge(yqs[lane], neg_bits(td));
+        byp = fma(bsm[nbv[nsl[lane]] - n], yqs[lane], byp);
       }
-      {
-        float dl[4] = {0.f, 0.f, 0.f, 0.f}, mg[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 2
-        for (int p = 0; p < kn; ++p) {         // reduced cost A_j^T y - c_j of every column
-          const int r = pick_slot(kp, p);
-          const float d = rrs[r];
-#pragma unroll
-          for (int s = 0; s < 4; ++s) {
-            const int j = lane + 32 * s;
-            if (j < n) {
-              const float a = a_row_f(p, j);
-              dl[s] = fmaf(a, d, dl[s]);
-              mg[s] = fmaf(fabsf(a), fabsf(d), mg[s]);
-            }
-          }
+      for (int j = lane; j < n; j += 32) {      // reduced cost A_j^T y - c_j of every column
+        float dl = 0.f, mg = 0.f;
+        for (int p = 0; p < kn; ++p) {
+          const float a = hi2f(reinterpret_cast<const unsigned *>(ar + p * n + j)[1]), d = rrs[nbv[nsl[p]] - n];
+          dl = fmaf(a, d, dl);
+          mg = fmaf(fabsf(a), fabsf(d), mg);
         }
-#pragma unroll
-        for (int s = 0; s < 4; ++s)
-          if (lane + 32 * s < n) fail |= !dge(dj[s] + f2d_exact(dl[s] - kDeltaErr * mg[s]), neg_bits(td));
+        fail |= !dge(djs[j] + f2d_exact(dl - kDeltaErr * mg), neg_bits(td));
       }
       cx = warp_sum(cxp);
       const double by = warp_sum(byp);
@@ -821,16 +723,14 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       __syncwarp();          // the scratch arrays are rewritten by the next round
     }
     if (!fail) {
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int j = lane + 32 * s;
-        if (j < n && nbv[j] < n) P.R.x[coff + nbv[j]] = 0.0;
-        if (unsigned(bv[s]) < unsigned(n)) P.R.x[coff + bv[s]] = xb[s];
-        if (P.R.y) {
-          if (bv[s] >= n) P.R.y[yoff + (bv[s] - n)] = 0.0;
-          if (lane + 32 * s < kn) P.R.y[yoff + kp[s]] = yq[s];
-        }
+      for (int j = lane; j < n; j += 32)
+        if (nbv[j] < n) P.R.x[coff + nbv[j]] = 0.0;
+      for (int t = lane; t < m; t += 32) {
+        const int v = bas[t];
+        if (v < n) P.R.x[coff + v] = xrow[t];
+        else if (P.R.y) P.R.y[yoff + (v - n)] = 0.0;
       }
+      if (P.R.y && lane < kn) P.R.y[yoff + (nbv[nsl[lane]] - n)] = yqs[lane];
     }
     if (lane == 0) {
       if (!fail) {
