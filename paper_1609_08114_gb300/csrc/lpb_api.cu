@@ -221,13 +221,13 @@ lpb_err warp_pass(const DeviceInfo &d, const lpb_batch *b, int lim_m, int lim_n,
 // shared-memory kernel: FP32 modes with FP64 input, the largest-coefficient or
 // random rule, no kernel shape asked for, m and n from 32 (smaller LPs go
 // several per warp) to where it is measured faster than the register kernel:
-// m n <= 8000 with the FP64 refinement (80 x 100, not 100 x 100), m, n <= 100
+// m n <= 8100 with the FP64 refinement (90 x 90, not 100 x 100), m, n <= 100
 // without.
 bool warp_auto(const lpb_batch *b, const lpb_options *o, int mode, int lim_m, int lim_n) {
   if (o->kernel != LPB_KERNEL_AUTO || o->threads != 0 || o->reg_warps != 0) return false;
   if (mode == MODE_FP64 || b->dtype != LPB_DTYPE_F64 || o->pivot_rule == LPB_PIVOT_STEEPEST) return false;
   if (!warp_fits(lim_m, lim_n) || (lim_m < 32 && lim_n < 32)) return false;
-  return mode == MODE_FP32 ? (lim_m <= 100 && lim_n <= 100) : lim_m * lim_n <= 8000;
+  return mode == MODE_FP32 ? (lim_m <= 100 && lim_n <= 100) : lim_m * lim_n <= 8100;
 }
 
 lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o, bool basis_given,

@@ -47,6 +47,7 @@ struct WarpLayout {
   int tab;        // bytes of the tableau region (the tableau, or more: see warp_layout)
   int colb;       // byte offsets of the small arrays
   int rr, dx, bas, nbv, sb, ns;
+  int bar;        // the warp's transaction barrier (8 bytes)
   int bytes;      // size of the region (a multiple of 16)
 };
 
@@ -66,7 +67,8 @@ __host__ __device__ inline WarpLayout warp_layout(int max_m, int max_n) {
   const int a8 = ((max_m > max_n ? max_m : max_n) + 1 + 7) & ~7;
   const int arrays = 20 * a8;
   int tab = (max_m + 1) * L.S * 4;   // the tableau (16-byte rows)
-  const int want = ((max_m * (kRefK | 1) * 4 + 15) & ~15) + (kRefK + 1) * (max_m + max_n) * 8;
+  const int want = ((max_m * (kRefK | 1) * 4 + 15) & ~15) + max_m * (kRefK | 1) * 8 + kRefK * max_n * 8 +
+                   (max_m + max_n) * 8 + (3 * max_m + max_n + 2 * kRefK) * 8 + 3 * kRefK * 4;
   const int room = ((232448 / kWarpMaxWarps - arrays) & ~15);
   if (want > tab && room > tab) tab = want < room ? (want + 15) & ~15 : room;
   L.tab = tab;
@@ -78,6 +80,8 @@ __host__ __device__ inline WarpLayout warp_layout(int max_m, int max_n) {
   L.nbv = off;  off += 2 * a8;
   L.sb = off;   off += 2 * a8;
   L.ns = off;   off += 2 * a8;
+  off = (off + 7) & ~7;
+  L.bar = off;  off += 8;
   L.bytes = (off + 15) & ~15;
   return L;
 }
@@ -240,6 +244,87 @@ __device__ __forceinline__ float vec_in(const void *v, long long i, int &bad, un
   return d2f_tile(d, bad);
 }
 
+// Outcome of the tableau build.
+enum : int { BUILD_BAD = 1, BUILD_TIMEOUT = 2 };
+constexpr int kBulkBuild = 7000;
+
+// The LP's FP64 A into the tableau's rows 0..m-1 as FP32.  When A is large
+// (BULK, the templates of more than 96 columns, and m n > kBulkBuild:
+// measured, below these plain loads finish sooner and the bulk path's code
+// only adds to the instruction footprint), starts on
+// a 16-byte boundary and its rows are whole 16-byte units (n even) no shorter
+// than a tableau row, rows arrive in rounds of bulk copies staged at the top
+// of the free part of the tableau region (`tab` bytes): a round stages as many
+// rows as fit above the rows already converted (one copy: the rows are
+// contiguous), the warp waits on its transaction barrier, then converts them
+// in order, two rows at a time, each pair read in full before it is written
+// and written below every staged row still unread (a tableau row is no longer
+// than an FP64 row).  Rows for which no round of at least four has room go by
+// plain loads.  A copy that does not land within kCopyWaitNs gives
+// BUILD_TIMEOUT (after ERR_WAIT_TIMEOUT, and ERR_COPY_IN_FLIGHT if it is still
+// outstanding kDrainWaitNs later): the warp must then stop using its region.
+template <bool BULK>
+__device__ __forceinline__ int build_a(const TableauParams &P, unsigned char *region, int tab, int S, int m, int n,
+                                       long long aoff, int lane, uint64_t *bar, unsigned &phase) {
+  const double *Ag = static_cast<const double *>(P.B.A) + aoff;
+  float *T = reinterpret_cast<float *>(region);
+  const int SB = S * 4, RB = n * 8;
+  unsigned amax = 0u;
+  int r0 = 0;
+  if (BULK && (reinterpret_cast<uintptr_t>(Ag) & 15) == 0 && (n & 1) == 0 && SB <= RB && m * n > kBulkBuild) {
+    const int h = n >> 1;                          // pairs per row
+    const float inv_h = 1.f / float(h);
+    for (;;) {
+      const int rows = min((tab - r0 * SB) / RB, m - r0);
+      if (rows <= 0 || (rows < 4 && rows < m - r0)) break;
+      const int stage = tab - rows * RB;
+      __syncwarp();
+      if (lane == 0) {
+        fence_async_smem();           // earlier reads and writes of the region before the copy's writes
+        mbar_expect_tx(bar, unsigned(rows * RB));
+        bulk_load(region + stage, Ag + static_cast<long long>(r0) * n, unsigned(rows * RB), bar);
+      }
+      const bool ok = mbar_wait_for(bar, phase, kCopyWaitNs);
+      phase ^= 1u;
+      if (__any_sync(kFull, !ok)) {
+        if (lane == 0) {
+          atomicOr(P.err, ERR_WAIT_TIMEOUT);
+          if (!mbar_wait_for(bar, phase ^ 1u, kDrainWaitNs)) atomicOr(P.err, ERR_COPY_IN_FLIGHT);
+        }
+        __syncwarp();
+        return BUILD_TIMEOUT;
+      }
+      const double2 *st = reinterpret_cast<const double2 *>(region + stage);
+      for (int g = 0; g < rows; g += 2) {
+        const int np = min(2, rows - g) * h;       // pairs of this group
+        double2 v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int pi = lane + 32 * t;
+          if (pi < np) v[t] = st[g * h + pi];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int pi = lane + 32 * t;
+          if (pi < np) {
+            const int rr = int((float(pi) + 0.5f) * inv_h);
+            float2 f;
+            f.x = d2f_trunc(v[t].x, amax);
+            f.y = d2f_trunc(v[t].y, amax);
+            *reinterpret_cast<float2 *>(T + (r0 + g + rr) * S + 2 * (pi - rr * h)) = f;
+          }
+        }
+      }
+      r0 += rows;
+      if (r0 >= m) break;
+    }
+    __syncwarp();
+  }
+  if (r0 < m) build_rows_ldg(T, S, Ag, r0, m, n, lane, amax);
+  return amax >= (1151u << 20) ? BUILD_BAD : 0;     // |a| >= 2^128, Inf or NaN
+}
+
 template <int U>
 __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauParams P, WarpLayout L) {
   extern __shared__ __align__(16) unsigned char warp_smem[];
@@ -264,6 +349,13 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
     if (threadIdx.x == 0) atomicOr(P.err, ERR_BAD_LAUNCH);
     return;
   }
+  uint64_t *bar = reinterpret_cast<uint64_t *>(base + L.bar);
+  unsigned bphase = 0;           // parity of the next completion of bar
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
   auto fits_lp = [&](int m, int n) {
     return m >= 1 && n >= 1 && m <= P.lim_m && n <= P.lim_n && m <= P.B.max_m && n <= P.B.max_n &&
            m <= kWarpMaxDim && n <= kWarpMaxDim && n + 1 <= 16 * U;
@@ -317,9 +409,21 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
     long long na = 0, nb = 0, nc = 0;
     if (nitem < nitems) read_desc(nitem, nlp, nm, nn, na, nb, nc);
     if (fits) {
-      unsigned amax = 0u;
-      build_rows_ldg(T, S, static_cast<const double *>(P.B.A) + aoff, 0, m, n, lane, amax);
-      bad |= int(amax >= (1151u << 20));     // |a| >= 2^128, Inf or NaN
+      const int br = build_a<(U >= 7)>(P, base, L.tab, S, m, n, aoff, lane, bar, bphase);
+      if (br & BUILD_TIMEOUT) {
+        // The copy engine did not deliver in time: this LP and the one claimed
+        // after it go to the shared-memory kernel, and the warp stops.
+        if (lane == 0) {
+          P.R.status[lp] = STATUS_PENDING;
+          list_push(P.defer_items, P.defer_count, P.list_cap, lp, P.err);
+          if (nitem < nitems) {
+            P.R.status[nlp] = STATUS_PENDING;
+            list_push(P.defer_items, P.defer_count, P.list_cap, nlp, P.err);
+          }
+        }
+        return;
+      }
+      bad |= br;
       // The right-hand side column, the objective row (-c, and 0 on the
       // right-hand side) and the zero columns n+1 .. 4 ceil((n+1)/4) - 1 that
       // the update sweeps.
@@ -548,15 +652,16 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
     // (A's basic columns, k x m column-major, and the non-basic slacks' rows,
     // k x n, gathered by asynchronous copies in one round trip with b and c),
     // then the FP64 state: x of each row's basic variable, b - A x and the
-    // residual by row, the reduced costs by column, y by non-basic slack.  An
-    // LP with more than kRefK basic structurals, or whose operands do not fit,
-    // goes to the FP64 re-solve instead.
-    const int ks = kn | 1;
+    // residual by row, the reduced costs by column, y by non-basic slack, and
+    // per-q / per-p values that the inner loops read by broadcast.  An LP with
+    // more than kRefK basic structurals, or whose operands do not fit, goes to
+    // the FP64 re-solve instead.
+    const int ks = kn | 1;                    // odd strides: no bank conflicts
     const int off_ac = (m * ks * 4 + 15) & ~15;
-    const int off_ar = off_ac + k * m * 8;
+    const int off_ar = off_ac + m * ks * 8;
     const int off_bc = off_ar + kn * n * 8;
     const int off_st = off_bc + (m + n) * 8;
-    if (kn > kRefK || off_st + (3 * m + n + kn) * 8 + kRefK * 4 > L.tab) {
+    if (kn > kRefK || off_st + (3 * m + n + 2 * kRefK) * 8 + 3 * kRefK * 4 > L.tab) {
       if (lane == 0) {
         P.R.status[lp] = STATUS_PENDING;
         if (P.R.iters) P.R.iters[lp] = iters;
@@ -572,7 +677,7 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
     for (int s = 0; s < 4; ++s) xf[s] = lane + 32 * s < m ? T[(lane + 32 * s) * S + n] : 0.f;
     if (lane < kn) yf = T[m * S + nsl[lane]];
     float *tcomp = T;                                                    // [m][ks]
-    double *ac = reinterpret_cast<double *>(base + off_ac);              // [k][m]
+    double *ac = reinterpret_cast<double *>(base + off_ac);              // [m][ks]: A[i, j_q]
     double *ar = reinterpret_cast<double *>(base + off_ar);              // [kn][n]
     double *bsm = reinterpret_cast<double *>(base + off_bc);             // b [m], then c [n]
     double *csm = bsm + m;
@@ -581,7 +686,10 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
     double *rrd = saxs + m;                                              // residual r by row
     double *djs = rrd + m;                                               // reduced cost by column
     double *yqs = djs + n;                                               // y of the p-th non-basic slack
-    float *coef = reinterpret_cast<float *>(yqs + kn);                   // r of the p-th non-basic slack
+    double *xq = yqs + kRefK;                                            // x of the q-th basic structural
+    float *coef = reinterpret_cast<float *>(xq + kRefK);                 // r of the p-th non-basic slack
+    float *dq = coef + kRefK;                                            // dx of the q-th basic structural
+    int *krl = reinterpret_cast<int *>(dq + kRefK);                      // row of A of the p-th non-basic slack
     // Compaction four rows at a time in row order, lane p taking column p:
     // compacted rows up to i end before tableau row i + 1 starts (ks < S), so
     // no row is overwritten unread.
@@ -600,9 +708,11 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
     }
     {
       const double *Ad = static_cast<const double *>(P.B.A) + aoff;
-      for (int q = 0; q < k; ++q) {
-        const int jq = bas[sbl[q]];
-        for (int i = lane; i < m; i += 32) cp_async8(ac + q * m + i, Ad + static_cast<long long>(i) * n + jq);
+      // A's basic columns row by row, lane q taking column j_q: one copy
+      // instruction per row touches only that row's lines.
+      if (lane < k) {
+        const double *src = Ad + bas[sbl[lane]];
+        for (int i = 0; i < m; ++i, src += n) cp_async8(ac + i * ks + lane, src);
       }
       for (int p = 0; p < kn; ++p) {
         const int r = nbv[nsl[p]] - n;
@@ -616,7 +726,10 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
 #pragma unroll
     for (int s = 0; s < 4; ++s)
       if (lane + 32 * s < m) xrow[lane + 32 * s] = f2d_exact(xf[s]);
-    if (lane < kn) yqs[lane] = f2d_exact(yf);
+    if (lane < kn) {
+      yqs[lane] = f2d_exact(yf);
+      krl[lane] = nbv[nsl[lane]] - n;
+    }
     cp_async_wait_all();
     __syncwarp();
     const double tol = P.feas_tol;
@@ -628,9 +741,11 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
     for (int round = 0;; ++round) {
       // Row residuals in FP64: b_i - sum_q A[i, j_q] x_q over the basic
       // structurals, and r_i: that minus x of slack i when it is basic.
+      if (lane < k) xq[lane] = xrow[sbl[lane]];
+      __syncwarp();
       for (int i = lane; i < m; i += 32) {
         double acc = 0.0;
-        for (int q = 0; q < k; ++q) acc = fma(ac[q * m + i], xrow[sbl[q]], acc);
+        for (int q = 0; q < k; ++q) acc = fma(ac[i * ks + q], xq[q], acc);
         saxs[i] = bsm[i] - acc;
         xs[i] = 0.0;
       }
@@ -653,7 +768,7 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       // rho_t = -d of the basic structural of row t (0 for a basic slack); the
       // residuals of the non-basic slacks, by p.
       for (int t = lane; t < m; t += 32) colb[t] = bas[t] < n ? dxs[bas[t]] : 0.f;
-      if (lane < kn) coef[lane] = rrs[nbv[nsl[lane]] - n];
+      if (lane < kn) coef[lane] = rrs[krl[lane]];
       __syncwarp();
       // Corrections with the FP32 basis inverse, whose column for slack k is the
       // tableau column of k when k is non-basic, else a unit vector:
@@ -677,8 +792,10 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
         if (t < m) a0 = fmaf(tcomp[t * ks + lane], colb[t], a0);
         const float dy = a0 + a1;
         yqs[lane] += f2d_exact(dy);
-        rrs[nbv[nsl[lane]] - n] = dy;          // dy by slack, for the certificate
+        coef[lane] = dy;                       // dy of the p-th non-basic slack, for the certificate
       }
+      __syncwarp();
+      if (lane < k) dq[lane] = dxs[sbl[lane]];
       __syncwarp();
       // KKT certificate of the pair that is written out (x: the structural part
       // of x_B; y: the slack duals): x >= 0, A x <= b, y >= 0, A^T y >= c and
@@ -696,7 +813,7 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
         }
         float dl = 0.f, mg = 0.f;
         for (int q = 0; q < k; ++q) {
-          const float a = hi2f(reinterpret_cast<const unsigned *>(ac + q * m + i)[1]), d = dxs[sbl[q]];
+          const float a = hi2f(reinterpret_cast<const unsigned *>(ac + i * ks + q)[1]), d = dq[q];
           dl = fmaf(a, d, dl);
           mg = fmaf(fabsf(a), fabsf(d), mg);
         }
@@ -704,12 +821,12 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       }
       if (lane < kn) {                          // y >= 0
         fail |= !dge(yqs[lane], neg_bits(td));
-        byp = fma(bsm[nbv[nsl[lane]] - n], yqs[lane], byp);
+        byp = fma(bsm[krl[lane]], yqs[lane], byp);
       }
       for (int j = lane; j < n; j += 32) {      // reduced cost A_j^T y - c_j of every column
         float dl = 0.f, mg = 0.f;
         for (int p = 0; p < kn; ++p) {
-          const float a = hi2f(reinterpret_cast<const unsigned *>(ar + p * n + j)[1]), d = rrs[nbv[nsl[p]] - n];
+          const float a = hi2f(reinterpret_cast<const unsigned *>(ar + p * n + j)[1]), d = coef[p];
           dl = fmaf(a, d, dl);
           mg = fmaf(fabsf(a), fabsf(d), mg);
         }
@@ -730,7 +847,7 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
         if (v < n) P.R.x[coff + v] = xrow[t];
         else if (P.R.y) P.R.y[yoff + (v - n)] = 0.0;
       }
-      if (P.R.y && lane < kn) P.R.y[yoff + (nbv[nsl[lane]] - n)] = yqs[lane];
+      if (P.R.y && lane < kn) P.R.y[yoff + krl[lane]] = yqs[lane];
     }
     if (lane == 0) {
       if (!fail) {

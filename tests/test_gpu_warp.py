@@ -138,7 +138,7 @@ def test_many_basic_structurals_go_to_the_fp64_resolve(solver):
 
 def test_planner_picks_it_for_mid_sizes(solver):
     """The default plan for uniform FP64 batches (the size hint min = max given): the warp
-    kernel for m n <= 8000, the register kernel for m = n = 100; parity both ways."""
+    kernel for m n <= 8100, the register kernel for m = n = 100; parity both ways."""
     for (m, n) in ((64, 64), (100, 100)):
         sb = synth.type1(200, m, n, seed=3)
         dev = to_device(sb)
