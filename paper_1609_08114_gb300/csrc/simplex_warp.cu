@@ -69,7 +69,7 @@ __host__ __device__ inline WarpLayout warp_layout(int max_m, int max_n) {
   int tab = (max_m + 1) * L.S * 4;   // the tableau (16-byte rows)
   const int want = ((max_m * (kRefK | 1) * 4 + 15) & ~15) + max_m * (kRefK | 1) * 8 + kRefK * max_n * 8 +
                    (max_m + max_n) * 8 + (3 * max_m + max_n + 2 * kRefK) * 8 + 3 * kRefK * 4;
-  const int room = ((232448 / kWarpMaxWarps - arrays) & ~15);
+  const int room = ((232448 / kWarpMaxWarps - arrays - 16) & ~15);   // 16: the barrier, aligned
   if (want > tab && room > tab) tab = want < room ? (want + 15) & ~15 : room;
   L.tab = tab;
   int off = tab;
