@@ -43,7 +43,7 @@ namespace {
 constexpr int kMaxThreads = 1024;
 
 struct Layout {
-  size_t tab, colb, rowb, basic, nonb, redv, redk, rcp, redf, sel, ins, wl, xb, rr, yv, rho, sb, ns, sp, dj, jq, kq, total;
+  size_t tab, colb, rowb, gam, basic, nonb, redv, redk, rcp, redf, sel, ins, wl, xb, rr, yv, rho, sb, ns, sp, dj, jq, kq, total;
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -64,6 +64,7 @@ __host__ __device__ inline Layout make_layout(int eb, size_t tab, int max_m, int
   L.tab = o;   o = align16(o + tab);
   L.colb = o;  o = align16(o + rows * eb);
   L.rowb = o;  o = align16(o + ld * eb);
+  L.gam = o;   o = align16(o + ld * eb);
   L.basic = o; o = align16(o + size_t(max_m) * 4);
   L.nonb = o;  o = align16(o + ld * 4);
   L.redv = o;  o = align16(o + 64 * size_t(eb));
@@ -100,6 +101,7 @@ struct Tab {
   T *tg;          // rows rs.. in the CTA's workspace slot
   int rs;
   T *colb, *rowb;
+  T *gam;         // steepest edge: gamma_j of every column
   int *basic, *nonb;
   T *redv;
   int *redk;
@@ -157,6 +159,18 @@ __device__ __forceinline__ float4 scale_vec(float4 pr, float rp) {
 __device__ __forceinline__ double2 scale_vec(double2 pr, double rp) {
   return make_double2(pr.x * rp, pr.y * rp);
 }
+// acc + x * x, elementwise (steepest-edge weights), and the elements of a vector.
+__device__ __forceinline__ float4 sq_acc(float4 acc, float4 x) {
+  return make_float4(fmaf(x.x, x.x, acc.x), fmaf(x.y, x.y, acc.y), fmaf(x.z, x.z, acc.z), fmaf(x.w, x.w, acc.w));
+}
+__device__ __forceinline__ double2 sq_acc(double2 acc, double2 x) {
+  return make_double2(fma(x.x, x.x, acc.x), fma(x.y, x.y, acc.y));
+}
+__device__ __forceinline__ float vec_el(float4 v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vec_el(double2 v, int c) { return c == 0 ? v.x : v.y; }
+template <typename V> __device__ __forceinline__ V vec_zero();
+template <> __device__ __forceinline__ float4 vec_zero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ double2 vec_zero<double2>() { return make_double2(0.0, 0.0); }
 
 // Step 3 on the calling warp's rows: with rp = 1 / t_le, every row i != l
 // becomes row_i - (t_ie rp) row_l and its column e -t_ie rp; the warp owning
@@ -166,9 +180,12 @@ __device__ __forceinline__ double2 scale_vec(double2 pr, double rp) {
 // vectors: a lane keeps its vectors of the pivot row in registers while the
 // warp's rows stream past, so each row's multiplier and address are read once
 // per chunk and the kJ loads of a row are in flight together.  Column e is
-// written by a scalar pass after the vector sweep.
-template <typename T, int kJ>
-__device__ __forceinline__ void pivot_update(const Tab<T> &S_, int rows, int l, int e, T rp) {
+// written by a scalar pass after the vector sweep.  SE: the sweep also adds
+// the squares of the values it writes in the constraint rows in use (phase 2
+// skips rows whose basic variable is artificial) to gamma_j in S.gam (zero on
+// entry), with the scaled pivot row's; column e's gamma is left to the caller.
+template <typename T, int kJ, bool SE>
+__device__ __forceinline__ void pivot_update(const Tab<T> &S_, int rows, int l, int e, T rp, int phase) {
   const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
   using V = typename Vec<T>::type;
   constexpr int NV = Vec<T>::N;
@@ -185,12 +202,17 @@ __device__ __forceinline__ void pivot_update(const Tab<T> &S_, int rows, int l, 
   for (int j0 = lane; j0 < nv; j0 += 32 * kJ) {
     // Vectors past the row's end stand in as j0 (loaded, never stored).
     int jj[kJ];
-    V pr[kJ];
+    V pr[kJ], acc[kJ];
 #pragma unroll
     for (int k = 0; k < kJ; ++k) {
       jj[k] = j0 + 32 * k < nv ? j0 + 32 * k : j0;
       pr[k] = prow[jj[k]];
-      if (own_l && j0 + 32 * k < nv) rowb[jj[k]] = scale_vec(pr[k], rp);
+      acc[k] = vec_zero<V>();
+      if (own_l && j0 + 32 * k < nv) {
+        const V sr = scale_vec(pr[k], rp);
+        rowb[jj[k]] = sr;
+        if (SE) acc[k] = sq_acc(acc[k], sr);      // row l is in use after the pivot
+      }
     }
     for (int i = r0; i < r1; ++i) {
       if (i == l) continue;
@@ -199,9 +221,24 @@ __device__ __forceinline__ void pivot_update(const Tab<T> &S_, int rows, int l, 
       V v[kJ];
 #pragma unroll
       for (int k = 0; k < kJ; ++k) v[k] = rw[jj[k]];
+      const bool use = SE && i < S.m && !(phase == 2 && S.basic[i] >= S.nm);
 #pragma unroll
       for (int k = 0; k < kJ; ++k)
-        if (j0 + 32 * k < nv) rw[jj[k]] = upd_vec(v[k], pr[k], nf);
+        if (j0 + 32 * k < nv) {
+          const V u = upd_vec(v[k], pr[k], nf);
+          rw[jj[k]] = u;
+          if (use) acc[k] = sq_acc(acc[k], u);
+        }
+    }
+    if (SE) {
+#pragma unroll
+      for (int k = 0; k < kJ; ++k)
+        if (j0 + 32 * k < nv)
+#pragma unroll
+          for (int c = 0; c < NV; ++c) {
+            const int col = (j0 + 32 * k) * NV + c;
+            if (col < S.nc) atomicAdd(S.gam + col, vec_el(acc[k], c));
+          }
     }
   }
   __syncwarp();                           // the vector stores of this warp's rows are done
@@ -228,10 +265,11 @@ __device__ __forceinline__ void pivot_finish(const Tab<T> &S_, int rows, int l) 
   __syncwarp();
 }
 
-template <typename T>
-__device__ __forceinline__ void update_any(const Tab<T> &S_, int rows, int l, int e, T rp) {
+template <typename T, bool SE = false>
+__device__ __forceinline__ void update_any(const Tab<T> &S_, int rows, int l, int e, T rp, int phase = 2) {
   const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
-  pivot_update<T, sizeof(T) == 4 ? 3 : 2>(S, rows, l, e, rp);
+  // Fewer vectors per lane under steepest edge: its accumulators take the registers.
+  pivot_update<T, SE ? (sizeof(T) == 4 ? 2 : 1) : (sizeof(T) == 4 ? 3 : 2), SE>(S, rows, l, e, rp, phase);
 }
 
 // A whole pivot on (l, e) for the callers outside the Step 1-3 loop (Phase-I
@@ -253,25 +291,28 @@ __device__ __forceinline__ void pivot(const Tab<T> &S_, int rows, int l, int e) 
   __syncthreads();
 }
 
-// Steepest-edge weights gamma_j = 1 + sum_i t_ij^2 of the columns eligible on
-// objective row `orow` (r_j < -eps_d, not artificial), summed over the
+// Steepest-edge weights gamma_j = 1 + sum_i t_ij^2, summed over the
 // constraint rows in row order with one fused multiply-add each (phase 2
 // skips rows whose basic variable is artificial: redundant rows left after
-// Phase I), into S.rowb, which is free between pivots.  Every thread takes
-// columns; the caller places a barrier before (rows final) and after.
+// Phase I), into S.gam: of every non-artificial column (`all`: the FP32
+// kernel, once when a phase starts, after which its pivots keep them), or of
+// the columns eligible on objective row `orow` (the FP64 kernel, before every
+// pivot: its weights follow the oracle's summation order exactly).  Every
+// thread takes columns; the caller places a barrier before (rows final) and
+// after.
 template <typename T>
-__device__ __forceinline__ void se_weights(const Tab<T> &S_, int orow, int phase, T eps_d) {
+__device__ __forceinline__ void se_weights(const Tab<T> &S_, int orow, int phase, T eps_d, bool all) {
   const Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
   const T *r = S.row(orow);
   for (int j = threadIdx.x; j < S.nc; j += blockDim.x) {
-    if (S.nonb[j] >= S.nm || !(r[j] < -eps_d)) continue;
+    if (S.nonb[j] >= S.nm || !(all || r[j] < -eps_d)) continue;
     T g = T(1);
     for (int i = 0; i < S.m; ++i) {
       if (phase == 2 && S.basic[i] >= S.nm) continue;
       const T t = S.at(i, j);
       g = fma(t, t, g);
     }
-    S.rowb[j] = g;
+    S.gam[j] = g;
   }
 }
 
@@ -279,7 +320,7 @@ __device__ __forceinline__ void se_weights(const Tab<T> &S_, int orow, int phase
 // eligible columns are those with a reduced cost below -eps_d; the most
 // negative one enters (LPC), or the one with the smallest random key at pivot
 // `it` (RPC), or the one with the largest r_j^2 / gamma_j (steepest edge, the
-// weights in S.rowb), or the lowest variable index under Bland's rule.  Column
+// weights in S.gam), or the lowest variable index under Bland's rule.  Column
 // `ecol` is taken to hold variable `evar` (a pivot whose swap of nonb may not
 // be visible yet).  Keys are (variable << kIdxBits) | column.
 template <typename T>
@@ -316,7 +357,7 @@ __device__ __forceinline__ void step1_warp(const Tab<T> &S_, int orow, bool blan
         const int var = j == ecol ? evar : S.nonb[j];
         if (var >= S.nm || !(r[j] < -eps_d)) continue;
         const float r32 = d2f_rn(r[j]);
-        b32 = fmaxf(b32, __fdiv_rn(r32 * r32, d2f_rn(S.rowb[j])));
+        b32 = fmaxf(b32, __fdiv_rn(r32 * r32, d2f_rn(S.gam[j])));
       }
       b32 = __uint_as_float(__reduce_max_sync(kFull, __float_as_uint(b32)));   // >= 0: bits order like values
       cut = isfinite(b32) ? b32 * (1.f - 1e-5f) : 0.f;
@@ -328,9 +369,9 @@ __device__ __forceinline__ void step1_warp(const Tab<T> &S_, int orow, bool blan
       if (!(rj < -eps_d)) continue;
       if constexpr (sizeof(T) == 8) {
         const float r32 = d2f_rn(rj);
-        if (__fdiv_rn(r32 * r32, d2f_rn(S.rowb[j])) < cut) continue;
+        if (__fdiv_rn(r32 * r32, d2f_rn(S.gam[j])) < cut) continue;
       }
-      keep_better(v, key, -((rj * rj) / S.rowb[j]), (var << kIdxBits) | j);
+      keep_better(v, key, -((rj * rj) / S.gam[j]), (var << kIdxBits) | j);
     }
     warp_argmin(v, key);
     return;
@@ -360,7 +401,10 @@ __device__ __forceinline__ void drop_column(Tab<T> &S, int rows, int e, bool rem
     r[S.nc] = T(0);
   }
   if (threadIdx.x == 0) {
-    if (e != last) S.nonb[e] = S.nonb[last];
+    if (e != last) {
+      S.nonb[e] = S.nonb[last];
+      S.gam[e] = S.gam[last];
+    }
     if (remap) {
       const int k = S.sel[0];
       if (k != INT_MAX && (k & kIdxMask) == last) S.sel[0] = (k & ~kIdxMask) | e;
@@ -388,12 +432,17 @@ __device__ __forceinline__ int run_phase(Tab<T> &S_, int orow, int rows, int pha
   const int per = (rows + nw - 1) / nw;
   const bool obj_warp = orow >= r0 && orow < r1;
   // Steepest edge needs every row of the updated tableau for its weights, so
-  // its Step 1 follows the pivot's last barrier instead of overlapping it.
+  // its Step 1 follows the pivot's barrier instead of overlapping it.  The
+  // FP32 kernel forms the weights once here and its pivots' sweeps keep them
+  // (every row adds its part of each column's gamma, by shared-memory atomics
+  // in no fixed order); the FP64 kernel re-sums them in row order before each
+  // pivot, so that it follows the oracle's choices.
   const bool se = rule == LPB_PIVOT_STEEPEST;
+  constexpr bool kFuse = sizeof(T) == 4;
   int degenerate_run = 0;
   bool bland = false;
   if (se) {
-    se_weights(S, orow, phase, eps_d);
+    se_weights(S, orow, phase, eps_d, kFuse);
     __syncthreads();
   }
   if (w == 0) {            // Step 1 of the first pivot
@@ -410,6 +459,10 @@ __device__ __forceinline__ int run_phase(Tab<T> &S_, int orow, int rows, int pha
       return done(LPB_OPTIMAL);
     }
     const int e = ekey & kIdxMask;
+    // Fused steepest edge: the weights are re-summed by this pivot's sweep
+    // (Step 1 of this pivot has read them).
+    if (kFuse && se)
+      for (int j = threadIdx.x; j < S.nc; j += blockDim.x) S.gam[j] = T(0);
     // Step 2 on this warp's rows, and the reciprocal of its best pivot.
     {
       T v = pos_inf<T>();
@@ -476,7 +529,12 @@ __device__ __forceinline__ int run_phase(Tab<T> &S_, int orow, int rows, int pha
       S.basic[l] = S.nonb[e];
       S.nonb[e] = leave;
     }
-    update_any(S, rows, l, e, rp);
+    if constexpr (kFuse) {
+      if (se) update_any<T, true>(S, rows, l, e, rp, phase);
+      else update_any(S, rows, l, e, rp);
+    } else {
+      update_any(S, rows, l, e, rp);
+    }
     ++iters;
     if (theta <= eps_p) {
       if (++degenerate_run >= S.m + S.n) bland = true;
@@ -492,15 +550,25 @@ __device__ __forceinline__ int run_phase(Tab<T> &S_, int orow, int rows, int pha
       if (lane == 0) S.sel[0] = key;
     }
     __syncthreads();
+    if (kFuse && se && w == 0) {   // gamma of column e, now the leaving variable's: -t_ie / p, and 1/p at row l
+      T g = T(0);
+      for (int i = lane; i < S.m; i += 32)
+        if (i != l && !(phase == 2 && S.basic[i] >= S.nm)) g = fma(S.colb[i], S.colb[i], g);
+      g = warp_sum(g);
+      if (lane == 0) S.gam[e] = T(1) + g + rp * rp;
+      __syncwarp();
+    }
     pivot_finish(S, rows, l);
     if (phase == 1 && leave >= S.nm) {   // the artificial's new column is dead
       __syncthreads();                   // the pivot row is in place
       drop_column(S, rows, e, true);
     }
-    if (se) {
-      __syncthreads();       // the pivot row is in place
-      se_weights(S, orow, phase, eps_d);
-      __syncthreads();
+    if (se) {                // Step 1 of the next pivot on the updated objective row and weights
+      if (!kFuse) {
+        __syncthreads();     // the pivot row is in place
+        se_weights(S, orow, phase, eps_d, false);
+        __syncthreads();
+      }
       if (w == 0) {
         T v;
         int key;
@@ -953,6 +1021,7 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
                       : nullptr;
   S.colb = reinterpret_cast<T *>(smem + L.colb);
   S.rowb = reinterpret_cast<T *>(smem + L.rowb);
+  S.gam = reinterpret_cast<T *>(smem + L.gam);
   S.basic = reinterpret_cast<int *>(smem + L.basic);
   S.nonb = reinterpret_cast<int *>(smem + L.nonb);
   S.redv = reinterpret_cast<T *>(smem + L.redv);
