@@ -18,10 +18,12 @@
 //   * Step 3: lane (r, g) = (lane mod 8, lane / 8) updates rows r + 8t and
 //     16-byte column blocks g + 4u (u < U): the pivot row's U blocks stay in
 //     registers, the rows stream past with the next row's loads in flight
-//     while the current row is written.  The update is bound by the shared-
-//     memory bandwidth: 2 (m + 1)(n + 1) 4 bytes per pivot.
-//   * The next LP's A, b and c are prefetched into L2 while this LP pivots,
-//     and the tableau is built from them with 16-byte loads.
+//     while the current row is written: 2 (m + 1)(n + 1) 4 bytes of shared
+//     memory per pivot.  With at most eight warps per SM (the register file)
+//     the kernel is bound by latency, not by that bandwidth.
+//   * The next LP's A, b and c are prefetched into L2 while this LP pivots;
+//     the tableau is built from them with 16-byte loads, or (large LPs in the
+//     wide templates) from rows staged by bulk copies.
 //   * Refinement and certificate as in the register kernel (FP64 residuals,
 //     one correction with the FP32 basis inverse, KKT certificate), on
 //     operands gathered into the dead tableau region: the non-basic slacks'
@@ -248,12 +250,12 @@ __device__ __forceinline__ float vec_in(const void *v, long long i, int &bad, un
 enum : int { BUILD_BAD = 1, BUILD_TIMEOUT = 2 };
 constexpr int kBulkBuild = 7000;
 
-// The LP's FP64 A into the tableau's rows 0..m-1 as FP32.  When A is large
-// (BULK, the templates of more than 96 columns, and m n > kBulkBuild:
-// measured, below these plain loads finish sooner and the bulk path's code
-// only adds to the instruction footprint), starts on
-// a 16-byte boundary and its rows are whole 16-byte units (n even) no shorter
-// than a tableau row, rows arrive in rounds of bulk copies staged at the top
+// The LP's FP64 A into the tableau's rows 0..m-1 as FP32.  In the templates
+// of more than 96 columns (BULK), for an LP of more than kBulkBuild entries
+// whose A starts on a 16-byte boundary with rows of whole 16-byte units (n
+// even) no shorter than a tableau row, rows arrive in rounds of bulk copies
+// (below these, plain loads finish sooner and the bulk path's code only adds
+// to the instruction footprint: measured), staged at the top
 // of the free part of the tableau region (`tab` bytes): a round stages as many
 // rows as fit above the rows already converted (one copy: the rows are
 // contiguous), the warp waits on its transaction barrier, then converts them
