@@ -38,11 +38,13 @@ def _check(solver, sb, prec, ref=None, **kw):
 
 
 @pytest.mark.parametrize("m,n", [(33, 33), (40, 70), (70, 40), (64, 64), (100, 100), (127, 127), (127, 32),
-                                 (32, 127), (1, 40), (40, 1), (2, 99), (99, 3)])
+                                 (32, 127), (1, 40), (40, 1), (2, 99), (99, 3), (127, 100), (110, 96), (101, 100)])
 @pytest.mark.parametrize("prec", ["fp32_refine", "fp32"])
 def test_shapes(solver, m, n, prec):
     """Shapes at and near the kernel's limits: odd and even n (16-byte or single loads in
-    the build), row counts that leave a partial last slot of the sweep, one row or column."""
+    the build), row counts that leave a partial last slot of the sweep, one row or column,
+    and LPs above 7,000 entries with even n in the wide templates, whose rows arrive in
+    rounds of bulk copies with different last rounds (127 x 100, 110 x 96, 101 x 100)."""
     sb = synth.type1(120, m, n, seed=100 + m + 3 * n)
     got = _check(solver, sb, prec)
     assert np.all(got["status"] == 0)
