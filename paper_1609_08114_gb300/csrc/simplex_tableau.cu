@@ -418,7 +418,7 @@ __device__ __forceinline__ void drop_column(Tab<T> &S, int rows, int e, bool rem
 // Phase 1 also ratio-tests rows whose basic variable is artificial; phase 2
 // skips them (they are redundant rows left after Phase I).  Phase 1 drops the
 // columns of artificials that leave the basis; S_.nc returns the new width.
-template <typename T>
+template <typename T, bool FUSE>
 __device__ __forceinline__ int run_phase(Tab<T> &S_, int orow, int rows, int phase, int &iters, int max_iter,
                          T eps_p, T eps_d, int rule, unsigned long long seed, long long lp) {
   Tab<T> S = S_;   // a register copy: stores through tableau pointers cannot alias it
@@ -433,12 +433,14 @@ __device__ __forceinline__ int run_phase(Tab<T> &S_, int orow, int rows, int pha
   const bool obj_warp = orow >= r0 && orow < r1;
   // Steepest edge needs every row of the updated tableau for its weights, so
   // its Step 1 follows the pivot's barrier instead of overlapping it.  The
-  // FP32 kernel forms the weights once here and its pivots' sweeps keep them
-  // (every row adds its part of each column's gamma, by shared-memory atomics
-  // in no fixed order); the FP64 kernel re-sums them in row order before each
-  // pivot, so that it follows the oracle's choices.
+  // FP32 kernel's steepest-edge instantiation (FUSE) forms the weights once
+  // here and its pivots' sweeps keep them (every row adds its part of each
+  // column's gamma, by shared-memory atomics in no fixed order); the FP64
+  // kernel re-sums them in row order before each pivot, so that it follows
+  // the oracle's choices.  The other rules' kernels carry none of the fused
+  // code.
   const bool se = rule == LPB_PIVOT_STEEPEST;
-  constexpr bool kFuse = sizeof(T) == 4;
+  constexpr bool kFuse = FUSE;
   int degenerate_run = 0;
   bool bland = false;
   if (se) {
@@ -1009,8 +1011,10 @@ __device__ __forceinline__ bool refine_and_verify(const Tab<float> &S_, const Ba
   return true;
 }
 
-template <typename T>
+// FUSE_SE: the FP32 steepest-edge instantiation (see run_phase).
+template <typename T, bool FUSE_SE>
 __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
+  constexpr bool kFuseSE = FUSE_SE;
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, nt = blockDim.x;
   const bool refine = (P.mode == MODE_FP32_REFINE) && sizeof(T) == 4;
@@ -1137,7 +1141,7 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
           const int jm = row_argmax_abs(S, m + 1, T(0), 0);
           if (jm >= 0) eps_d1 = eps_d * fmaxf(1.f, fabsf(S.at(m + 1, jm)));
         }
-        status = run_phase(S, m + 1, m + 2, 1, iters, max_iter, eps_p, eps_d1, P.rule, P.seed, P.lp_base + lp);
+        status = run_phase<T, kFuseSE>(S, m + 1, m + 2, 1, iters, max_iter, eps_p, eps_d1, P.rule, P.seed, P.lp_base + lp);
         if (status == LPB_OPTIMAL) {
           const double w = double(S.at(m + 1, S.nc));
           if (-w > ftol) {
@@ -1156,7 +1160,7 @@ __global__ void __launch_bounds__(kMaxThreads) tableau_kernel(TableauParams P) {
           }
         }
       }
-      if (status == LPB_OPTIMAL) status = run_phase(S, m, m + 1, 2, iters, max_iter, eps_p, eps_d, P.rule, P.seed, P.lp_base + lp);
+      if (status == LPB_OPTIMAL) status = run_phase<T, kFuseSE>(S, m, m + 1, 2, iters, max_iter, eps_p, eps_d, P.rule, P.seed, P.lp_base + lp);
     }
     if constexpr (sizeof(T) == 4) if (P.mode == MODE_FP32_REFINE) {
       bool done = false;
@@ -1192,26 +1196,28 @@ size_t tableau_fixed_bytes(int eb, int max_m, int max_n, int kcap, bool refine) 
 
 size_t tableau_row_bytes(int eb, int max_n, int kcap) { return size_t(tab_ld(max_n, kcap, eb)) * size_t(eb); }
 
-template <typename T>
+template <typename T, bool SE>
 static cudaError_t prep(size_t smem) {
-  return cudaFuncSetAttribute(tableau_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  return cudaFuncSetAttribute(tableau_kernel<T, SE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
 }
 
 cudaError_t tableau_max_ctas_per_sm(int eb, int threads, size_t smem, int *ctas) {
   if (eb == 8) {
-    const cudaError_t e = prep<double>(smem);
-    return e != cudaSuccess ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, tableau_kernel<double>, threads, smem);
+    const cudaError_t e = prep<double, false>(smem);
+    return e != cudaSuccess ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, tableau_kernel<double, false>, threads, smem);
   }
-  const cudaError_t e = prep<float>(smem);
-  return e != cudaSuccess ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, tableau_kernel<float>, threads, smem);
+  const cudaError_t e = prep<float, false>(smem);
+  return e != cudaSuccess ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, tableau_kernel<float, false>, threads, smem);
 }
 
 cudaError_t launch_tableau(const TableauParams &p, bool fp64, int grid, int threads, size_t smem, cudaStream_t s) {
   if (threads < 32 || threads > kMaxThreads || (threads & 31) || grid < 1) return cudaErrorInvalidValue;
-  const cudaError_t e = fp64 ? prep<double>(smem) : prep<float>(smem);
+  const bool se = !fp64 && p.rule == LPB_PIVOT_STEEPEST;
+  const cudaError_t e = fp64 ? prep<double, false>(smem) : se ? prep<float, true>(smem) : prep<float, false>(smem);
   if (e != cudaSuccess) return e;
-  if (fp64) tableau_kernel<double><<<grid, threads, smem, s>>>(p);
-  else tableau_kernel<float><<<grid, threads, smem, s>>>(p);
+  if (fp64) tableau_kernel<double, false><<<grid, threads, smem, s>>>(p);
+  else if (se) tableau_kernel<float, true><<<grid, threads, smem, s>>>(p);
+  else tableau_kernel<float, false><<<grid, threads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
