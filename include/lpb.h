@@ -113,7 +113,9 @@ typedef struct {
   int32_t reg_warps;         /* warps per LP of the register kernel: 1 (m, n <= 31), 4 or 8
                                 [autotuned, else 1 when every LP has m, n <= 31, else 8; with
                                 kernel = AUTO and reg_warps = 0, batches of LPs with m, n <= 31
-                                take the several-LPs-per-warp kernel (LPB_KERNEL_PACK)] */
+                                take the several-LPs-per-warp kernel (LPB_KERNEL_PACK), and
+                                uniform FP64-input batches with 32 <= max(m, n) and m n <= 8100
+                                (plain FP32: m, n <= 100) take LPB_KERNEL_WARP] */
   int32_t pivot_rule;        /* lpb_pivot_rule: Step 1's entering-column rule [LPB_PIVOT_LPC] */
   uint64_t seed;             /* LPB_PIVOT_RPC: seed of the counter-based random draw [0] */
 } lpb_options;
@@ -199,9 +201,10 @@ lpb_err lpb_hyperbox(lpb_handle *handle, int64_t count, int32_t n, int32_t dtype
 
 /* Autotuner.  Picks, for batches shaped like `batch` (same max_m, max_n,
  * dtype and precision), the fastest schedule among: warps per LP of the
- * register kernel (1, 4 or 8), threads per CTA of the tableau kernel (automatic,
- * 256, 512 or 1024) and its placement (shared memory when it fits, or
- * L2-resident slots).
+ * register kernel (1, 4 or 8), the one-warp-per-LP shared-memory kernel
+ * (LPB_KERNEL_WARP, where it applies), threads per CTA of the tableau kernel
+ * (automatic, 256, 512 or 1024) and its placement (shared memory when it
+ * fits, or L2-resident slots).
  * If `table_path` (may be NULL) holds an entry for this shape, that entry is
  * loaded and nothing is timed; otherwise every candidate solves `batch` into
  * `result` on `stream` (one warm-up and two timed runs each, CUDA events),
