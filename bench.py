@@ -42,10 +42,11 @@ METRIC = "LPs/sec at m=n=100 (FP32+FP64-refine vs plain FP64, rel obj err<=1e-8)
 WORKLOAD = "type-1 LPs, 50,000 per GPU, m=n=100, A~U[0.1,1], b~U[1,10], c~U[0,1], seed 1"
 FP32_FMA_PIPES_PER_SM = 128
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per 50,000-LP launch of the
-# register-tableau kernel, from an ncu capture of a 5,000-LP launch scaled by 10 (DRAM bytes
-# grow with the LPs processed), keyed by the first 16 hex digits of the sha256 of the kernel
-# source it was taken on; a source without an entry reports traffic null.
-PROFILED_DRAM_BYTES = {"9f5fbb91b86f149f": 4189.3e6}
+# one-warp-per-LP kernel (the planner's choice at m = n = 100), from an ncu capture of a
+# 20,000-LP launch scaled by 2.5 (DRAM bytes grow with the LPs processed), keyed by the first
+# 16 hex digits of the sha256 of the kernel source it was taken on; a source without an entry
+# reports traffic null.
+PROFILED_DRAM_BYTES = {"96f21f8323b4d5d2": 8748.6e6}
 
 
 def parse():
@@ -166,12 +167,12 @@ class ClockSampler:
 
 
 def kernel_source_hash() -> str:
-    src = open(os.path.join(ROOT, "paper_1609_08114_gb300", "csrc", "simplex_reg.cu"), "rb").read()
+    src = open(os.path.join(ROOT, "paper_1609_08114_gb300", "csrc", "simplex_warp.cu"), "rb").read()
     return hashlib.sha256(src).hexdigest()[:16]
 
 
 def profiled_traffic():
-    """DRAM bytes per launch of the register kernel from the capture taken on this exact
+    """DRAM bytes per launch of the dominant kernel from the capture taken on this exact
     kernel source (PROFILED_DRAM_BYTES), else None."""
     return PROFILED_DRAM_BYTES.get(kernel_source_hash())
 
@@ -368,7 +369,7 @@ def main():
     barrier()
     ms_e2e = max_over_ranks(e0.elapsed_time(e1) / steps_e2e)
 
-    # roofline of the dominant kernel: the register-tableau launch (timing group 0)
+    # roofline of the dominant kernel: the first pass's launch (timing group 0)
     peaks, peak_src = {}, "fallback"
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))

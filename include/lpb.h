@@ -114,8 +114,10 @@ typedef struct {
                                 [autotuned, else 1 when every LP has m, n <= 31, else 8; with
                                 kernel = AUTO and reg_warps = 0, batches of LPs with m, n <= 31
                                 take the several-LPs-per-warp kernel (LPB_KERNEL_PACK), and
-                                uniform FP64-input batches with 32 <= max(m, n) and m n <= 8100
-                                (plain FP32: m, n <= 100) take LPB_KERNEL_WARP] */
+                                FP64-input batches (or size classes) with 32 <= max(m, n) take
+                                LPB_KERNEL_WARP up to m n = 10000, and beyond that where an SM
+                                holds four of its LPs (with refinement: while one register-kernel
+                                CTA per SM fits)] */
   int32_t pivot_rule;        /* lpb_pivot_rule: Step 1's entering-column rule [LPB_PIVOT_LPC] */
   uint64_t seed;             /* LPB_PIVOT_RPC: seed of the counter-based random draw [0] */
 } lpb_options;

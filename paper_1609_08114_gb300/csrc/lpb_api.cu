@@ -220,14 +220,27 @@ lpb_err warp_pass(const DeviceInfo &d, const lpb_batch *b, int lim_m, int lim_n,
 // Whether the planner gives LPs up to lim_m x lim_n the one-warp-per-LP
 // shared-memory kernel: FP32 modes with FP64 input, the largest-coefficient or
 // random rule, no kernel shape asked for, m and n from 32 (smaller LPs go
-// several per warp) to where it is measured faster than the register kernel:
-// m n <= 8100 with the FP64 refinement (90 x 90, not 100 x 100), m, n <= 100
-// without.
+// several per warp) up to where it is measured faster than the register
+// kernel (50,000 or 30,000 type-1 LPs): up to m n = 10,000 (100 x 100: 4.46
+// against 4.66 ms with the FP64 refinement), and beyond that where an SM holds
+// at least four of its regions while, with the refinement, the register kernel
+// fits one CTA per SM (110 x 100: 3.28 against 4.80 ms; 100 x 110, two register
+// CTAs per SM: 3.32 against 3.10; 127 x 127, three regions: 5.38 against 4.35).
 bool warp_auto(const lpb_batch *b, const lpb_options *o, int mode, int lim_m, int lim_n) {
   if (o->kernel != LPB_KERNEL_AUTO || o->threads != 0 || o->reg_warps != 0) return false;
   if (mode == MODE_FP64 || b->dtype != LPB_DTYPE_F64 || o->pivot_rule == LPB_PIVOT_STEEPEST) return false;
   if (!warp_fits(lim_m, lim_n) || (lim_m < 32 && lim_n < 32)) return false;
-  return mode == MODE_FP32 ? (lim_m <= 100 && lim_n <= 100) : lim_m * lim_n <= 8100;
+  if (lim_m * lim_n <= 10000) return true;
+  int wc = 0, wt = 0;
+  size_t ws = 0;
+  if (warp_occupancy(lim_m, lim_n, &wc, &wt, &ws) != cudaSuccess || wc * (wt / 32) < 4) return false;
+  if (mode == MODE_FP32) return true;
+  const int cfg = reg_pick(lim_m, lim_n, 8, false);
+  if (cfg < 0) return true;
+  int rc = 0, rt = 0;
+  size_t rs = 0;
+  if (reg_occupancy(cfg, lim_m, lim_n, b->dtype, o->pivot_rule, &rc, &rt, &rs) != cudaSuccess) return false;
+  return rc <= 1;
 }
 
 lpb_err make_plan(const DeviceInfo &d, const lpb_batch *b, const lpb_options *o, bool basis_given,

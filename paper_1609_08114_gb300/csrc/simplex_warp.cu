@@ -28,6 +28,13 @@
 //     one correction with the FP32 basis inverse, KKT certificate), on
 //     operands gathered into the dead tableau region: the non-basic slacks'
 //     tableau columns and the entries of A that the FP64 products read.
+//     Its row (column) loops take two rows (columns) per lane at a time, so
+//     two FP64 chains are in flight, in the same summation order per row.
+//   * Instruction footprint: eight warps in different phases of one large
+//     kernel share an SM's instruction caches, so every loop outside the
+//     pivot's hot path is kept rolled (`#pragma unroll 1`): 50,000 LPs of
+//     64 x 64 took 2.00 ms with those loops unrolled by the compiler and take
+//     1.53 ms rolled.
 //
 // Sizes beyond the launch's limits, LPs with some b_i < 0 (Phase I) and
 // non-finite data go to the shared-memory kernel, as from the register kernel.
@@ -444,6 +451,7 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       if (lane == 0) T[m * S + n] = 0.f;
       const int padw = 4 * ((n + 4) >> 2) - (n + 1);
       if (padw > 0)
+#pragma unroll 1
         for (int k = lane; k < (m + 1) * padw; k += 32) {
           const int i = k / padw;
           T[i * S + n + 1 + (k - i * padw)] = 0.f;
@@ -585,6 +593,7 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
     const int64_t yoff = P.R.y_off ? P.R.y_off[lp] : boff;    // outputs packed like b, or at y_off
     int32_t *bp = P.bbuf ? P.bbuf + (P.bpacked ? yoff : int64_t(lp) * P.B.max_m) : nullptr;
     if (bp)
+#pragma unroll 1
       for (int i = lane; i < m; i += 32) bp[i] = bas[i];
     if (status != LPB_OPTIMAL || P.mode != MODE_FP32_REFINE) {
       if (status == LPB_OPTIMAL) {           // plain FP32: results straight from the tableau
@@ -614,8 +623,10 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
           list_push(P.resolve_items, P.resolve_count, P.list_cap, lp, P.err);
         }
       } else {                                   // plain FP32: final as found
+#pragma unroll 1
         for (int j = lane; j < n; j += 32) P.R.x[coff + j] = 0.0;
         if (P.R.y)
+#pragma unroll 1
           for (int i = lane; i < m; i += 32) P.R.y[yoff + i] = 0.0;
         if (lane == 0) {
           P.R.status[lp] = status;
@@ -632,6 +643,7 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
     // Lists by ballot: sbl[q] is the row of the q-th basic structural, nsl[p]
     // the column of the p-th non-basic slack (as many as basic structurals).
     int k = 0, kn = 0;
+#pragma unroll 1
     for (int i0 = 0; i0 < m; i0 += 32) {
       const int i = i0 + lane;
       const bool in = i < m && bas[i] < n;
@@ -639,6 +651,7 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       if (in) sbl[k + __popc(mk & ((1u << lane) - 1u))] = short(i);
       k += __popc(mk);
     }
+#pragma unroll 1
     for (int j0 = 0; j0 < n; j0 += 32) {
       const int j = j0 + lane;
       const bool in = j < n && nbv[j] >= n;
@@ -697,6 +710,7 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
     // no row is overwritten unread.
     {
       const int c = lane < kn ? int(nsl[lane]) : 0;
+#pragma unroll 1
       for (int i0 = 0; i0 < m; i0 += 4) {
         float v[4];
 #pragma unroll
@@ -714,15 +728,20 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       // instruction per row touches only that row's lines.
       if (lane < k) {
         const double *src = Ad + bas[sbl[lane]];
+#pragma unroll 1
         for (int i = 0; i < m; ++i, src += n) cp_async8(ac + i * ks + lane, src);
       }
+#pragma unroll 1
       for (int p = 0; p < kn; ++p) {
         const int r = nbv[nsl[p]] - n;
+#pragma unroll 1
         for (int j = lane; j < n; j += 32) cp_async8(ar + p * n + j, Ad + static_cast<long long>(r) * n + j);
       }
       const double *bg = static_cast<const double *>(P.B.b) + boff;
       const double *cg64 = static_cast<const double *>(P.B.c) + coff;
+#pragma unroll 1
       for (int i = lane; i < m; i += 32) cp_async8(bsm + i, bg + i);
+#pragma unroll 1
       for (int j = lane; j < n; j += 32) cp_async8(csm + j, cg64 + j);
     }
 #pragma unroll
@@ -743,50 +762,91 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
     for (int round = 0;; ++round) {
       // Row residuals in FP64: b_i - sum_q A[i, j_q] x_q over the basic
       // structurals, and r_i: that minus x of slack i when it is basic.
+      // Here and below a lane takes rows (columns) i and i + 32 together; where
+      // i + 32 is past the end the second chain repeats row i and is dropped.
       if (lane < k) xq[lane] = xrow[sbl[lane]];
       __syncwarp();
-      for (int i = lane; i < m; i += 32) {
-        double acc = 0.0;
-        for (int q = 0; q < k; ++q) acc = fma(ac[i * ks + q], xq[q], acc);
-        saxs[i] = bsm[i] - acc;
+      for (int i = lane; i < m; i += 64) {
+        const int i2 = i + 32 < m ? i + 32 : i;
+        const double *a1 = ac + i * ks, *a2 = ac + i2 * ks;
+        double s1 = 0.0, s2 = 0.0;
+#pragma unroll 1
+        for (int q = 0; q < k; ++q) {
+          const double xv = xq[q];
+          s1 = fma(a1[q], xv, s1);
+          s2 = fma(a2[q], xv, s2);
+        }
+        saxs[i] = bsm[i] - s1;
         xs[i] = 0.0;
+        if (i2 != i) {
+          saxs[i2] = bsm[i2] - s2;
+          xs[i2] = 0.0;
+        }
       }
       __syncwarp();
+#pragma unroll 1
       for (int t = lane; t < m; t += 32)
         if (bas[t] >= n) xs[bas[t] - n] = xrow[t];
       __syncwarp();
+#pragma unroll 1
       for (int i = lane; i < m; i += 32) rrd[i] = saxs[i] - xs[i];
       __syncwarp();                           // xs (over colb and rr) is rewritten below
+#pragma unroll 1
       for (int i = lane; i < m; i += 32) rrs[i] = d2f_rn(rrd[i]);
       // Reduced costs in FP64: d_j = sum_p A[k_p, j] y_p - c_j.
-      for (int j = lane; j < n; j += 32) {
-        double acc = 0.0;
-        for (int p = 0; p < kn; ++p) acc = fma(ar[p * n + j], yqs[p], acc);
-        const double d = acc - csm[j];
+      for (int j = lane; j < n; j += 64) {
+        const int j2 = j + 32 < n ? j + 32 : j;
+        double s1 = 0.0, s2 = 0.0;
+#pragma unroll 1
+        for (int p = 0; p < kn; ++p) {
+          const double yv = yqs[p];
+          s1 = fma(ar[p * n + j], yv, s1);
+          s2 = fma(ar[p * n + j2], yv, s2);
+        }
+        const double d = s1 - csm[j];
         djs[j] = d;
         dxs[j] = d2f_rn(neg_bits(d));         // -d_j by column, for rho below
+        if (j2 != j) {
+          const double d2 = s2 - csm[j2];
+          djs[j2] = d2;
+          dxs[j2] = d2f_rn(neg_bits(d2));
+        }
       }
       __syncwarp();
       // rho_t = -d of the basic structural of row t (0 for a basic slack); the
       // residuals of the non-basic slacks, by p.
+#pragma unroll 1
       for (int t = lane; t < m; t += 32) colb[t] = bas[t] < n ? dxs[bas[t]] : 0.f;
       if (lane < kn) coef[lane] = rrs[krl[lane]];
       __syncwarp();
       // Corrections with the FP32 basis inverse, whose column for slack k is the
       // tableau column of k when k is non-basic, else a unit vector:
       //   dx_t = sum_p T[t, c_p] r_{k_p} (+ r of the slack itself in a basic slack's row).
-      for (int t = lane; t < m; t += 32) {
-        float acc = 0.f;
-        for (int p = 0; p < kn; ++p) acc = fmaf(tcomp[t * ks + p], coef[p], acc);
+      for (int t = lane; t < m; t += 64) {
+        const int t2 = t + 32 < m ? t + 32 : t;
+        float s1 = 0.f, s2 = 0.f;
+#pragma unroll 1
+        for (int p = 0; p < kn; ++p) {
+          const float cv = coef[p];
+          s1 = fmaf(tcomp[t * ks + p], cv, s1);
+          s2 = fmaf(tcomp[t2 * ks + p], cv, s2);
+        }
         const int v = bas[t];
-        const double d = f2d_exact(acc);
+        const double d = f2d_exact(s1);
         xrow[t] += v >= n ? d + rrd[v - n] : d;
-        dxs[t] = v < n ? acc : 0.f;            // the structural part of the correction
+        dxs[t] = v < n ? s1 : 0.f;             // the structural part of the correction
+        if (t2 != t) {
+          const int v2 = bas[t2];
+          const double d2 = f2d_exact(s2);
+          xrow[t2] += v2 >= n ? d2 + rrd[v2 - n] : d2;
+          dxs[t2] = v2 < n ? s2 : 0.f;
+        }
       }
       // dy_p = sum_t T[t, c_p] rho_t for the non-basic slacks (kn <= 32).
       if (lane < kn) {
         float a0 = 0.f, a1 = 0.f;
         int t = 0;
+#pragma unroll 1
         for (; t + 1 < m; t += 2) {
           a0 = fmaf(tcomp[t * ks + lane], colb[t], a0);
           a1 = fmaf(tcomp[(t + 1) * ks + lane], colb[t + 1], a1);
@@ -807,32 +867,54 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       // bounded by 2^-15 times the sum of the products' magnitudes.
       fail = 0;
       double cxp = 0.0, byp = 0.0;
-      for (int i = lane; i < m; i += 32) {      // x >= 0, and the slack b_i - A_i x of every row
+      for (int i = lane; i < m; i += 64) {      // x >= 0, and the slack b_i - A_i x of every row
+        const int i2 = i + 32 < m ? i + 32 : i;
+        const unsigned *h1 = reinterpret_cast<const unsigned *>(ac + i * ks) + 1;
+        const unsigned *h2 = reinterpret_cast<const unsigned *>(ac + i2 * ks) + 1;
+        float dl = 0.f, mg = 0.f, dl2 = 0.f, mg2 = 0.f;
+#pragma unroll 1
+        for (int q = 0; q < k; ++q) {
+          const float d = dq[q], ad = fabsf(d);
+          const float a = hi2f(h1[2 * q]), a2 = hi2f(h2[2 * q]);
+          dl = fmaf(a, d, dl);
+          mg = fmaf(fabsf(a), ad, mg);
+          dl2 = fmaf(a2, d, dl2);
+          mg2 = fmaf(fabsf(a2), ad, mg2);
+        }
         const int v = bas[i];
         if (v < n) {
           fail |= !dge(xrow[i], neg_bits(tp));
           cxp = fma(csm[v], xrow[i], cxp);
         }
-        float dl = 0.f, mg = 0.f;
-        for (int q = 0; q < k; ++q) {
-          const float a = hi2f(reinterpret_cast<const unsigned *>(ac + i * ks + q)[1]), d = dq[q];
-          dl = fmaf(a, d, dl);
-          mg = fmaf(fabsf(a), fabsf(d), mg);
-        }
         fail |= !dge(saxs[i] - f2d_exact(dl + kDeltaErr * mg), neg_bits(tp));
+        if (i2 != i) {
+          const int v2 = bas[i2];
+          if (v2 < n) {
+            fail |= !dge(xrow[i2], neg_bits(tp));
+            cxp = fma(csm[v2], xrow[i2], cxp);
+          }
+          fail |= !dge(saxs[i2] - f2d_exact(dl2 + kDeltaErr * mg2), neg_bits(tp));
+        }
       }
       if (lane < kn) {                          // y >= 0
         fail |= !dge(yqs[lane], neg_bits(td));
         byp = fma(bsm[krl[lane]], yqs[lane], byp);
       }
-      for (int j = lane; j < n; j += 32) {      // reduced cost A_j^T y - c_j of every column
-        float dl = 0.f, mg = 0.f;
+      for (int j = lane; j < n; j += 64) {      // reduced cost A_j^T y - c_j of every column
+        const int j2 = j + 32 < n ? j + 32 : j;
+        float dl = 0.f, mg = 0.f, dl2 = 0.f, mg2 = 0.f;
+#pragma unroll 1
         for (int p = 0; p < kn; ++p) {
-          const float a = hi2f(reinterpret_cast<const unsigned *>(ar + p * n + j)[1]), d = coef[p];
+          const unsigned *h = reinterpret_cast<const unsigned *>(ar + p * n) + 1;
+          const float d = coef[p], ad = fabsf(d);
+          const float a = hi2f(h[2 * j]), a2 = hi2f(h[2 * j2]);
           dl = fmaf(a, d, dl);
-          mg = fmaf(fabsf(a), fabsf(d), mg);
+          mg = fmaf(fabsf(a), ad, mg);
+          dl2 = fmaf(a2, d, dl2);
+          mg2 = fmaf(fabsf(a2), ad, mg2);
         }
         fail |= !dge(djs[j] + f2d_exact(dl - kDeltaErr * mg), neg_bits(td));
+        if (j2 != j) fail |= !dge(djs[j2] + f2d_exact(dl2 - kDeltaErr * mg2), neg_bits(td));
       }
       cx = warp_sum(cxp);
       const double by = warp_sum(byp);
@@ -842,8 +924,10 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       __syncwarp();          // the scratch arrays are rewritten by the next round
     }
     if (!fail) {
+#pragma unroll 1
       for (int j = lane; j < n; j += 32)
         if (nbv[j] < n) P.R.x[coff + nbv[j]] = 0.0;
+#pragma unroll 1
       for (int t = lane; t < m; t += 32) {
         const int v = bas[t];
         if (v < n) P.R.x[coff + v] = xrow[t];

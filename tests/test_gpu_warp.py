@@ -140,8 +140,10 @@ def test_many_basic_structurals_go_to_the_fp64_resolve(solver):
 
 def test_planner_picks_it_for_mid_sizes(solver):
     """The default plan for uniform FP64 batches (the size hint min = max given): the warp
-    kernel for m n <= 8100, the register kernel for m = n = 100; parity both ways."""
-    for (m, n) in ((64, 64), (100, 100)):
+    kernel up to m n = 10,000 and, beyond, where an SM holds four of its regions and one
+    register-kernel CTA (110 x 100), the register kernel otherwise (100 x 110, 127 x 127);
+    parity every way."""
+    for (m, n) in ((64, 64), (100, 100), (110, 100), (100, 110), (127, 127)):
         sb = synth.type1(200, m, n, seed=3)
         dev = to_device(sb)
         dev.min_m, dev.min_n = dev.max_m, dev.max_n
@@ -150,8 +152,9 @@ def test_planner_picks_it_for_mid_sizes(solver):
 
 
 def test_mixed_batch_class(solver):
-    """A mixed-size batch (m, n ~ U{3..127}): the size class up to 63 x 63 runs on the warp
-    kernel by default, the others on the register templates."""
+    """A mixed-size batch (m, n ~ U{3..127}): the size classes up to 63 x 63 and 127 x 103
+    run on the warp kernel by default, the smallest and the largest on the register
+    templates."""
     sb = synth.mixed_sizes(400, seed=12, lo=3, hi=127)
     got = host(solver.solve(to_device(sb), prec="fp32_refine"))
     compare(sb, got, obj_rtol=1e-8)
