@@ -21,9 +21,11 @@
 //     while the current row is written: 2 (m + 1)(n + 1) 4 bytes of shared
 //     memory per pivot.  With at most eight warps per SM (the register file)
 //     the kernel is bound by latency, not by that bandwidth.
-//   * The next LP's A, b and c are prefetched into L2 while this LP pivots;
-//     the tableau is built from them with 16-byte loads, or (large LPs in the
-//     wide templates) from rows staged by bulk copies.
+//   * The next LP's A, b and c are prefetched into L2 when this LP's pivots
+//     end (issued before the pivots, the lines were often evicted again by
+//     the time of the build: 100 x 100 4.46 -> 4.34 ms per 50,000 LPs with
+//     the later hint); the tableau is built from them with 16-byte loads, or
+//     (large LPs in the wide templates) from rows staged by bulk copies.
 //   * Refinement and certificate as in the register kernel (FP64 residuals,
 //     one correction with the FP32 basis inverse, KKT certificate), on
 //     operands gathered into the dead tableau region: the non-basic slacks'
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
 
   // Work items are claimed one LP ahead: the claim is issued when an LP
   // starts, the claimed LP's descriptor is read while this LP's tableau is
-  // built, and its data is prefetched into L2 before this LP's pivots.
+  // built, and its data is prefetched into L2 when this LP's pivots end.
   int item = 0;
   if (lane == 0) item = atomicAdd(P.queue, 1);
   item = __shfl_sync(kFull, item, 0);
@@ -458,7 +460,6 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
         }
     }
     bad = __any_sync(kFull, bad);
-    if (lane == 0 && nitem < nitems && !P.shared && fits_lp(nm, nn)) warp_prefetch(P, nm, nn, na, nb, nc);
     if (bad) {             // the shared-memory kernel handles it (Phase I, sizes, bad data)
       if (lane == 0) {
         P.R.status[lp] = STATUS_PENDING;
@@ -590,6 +591,8 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
       }
     }
 
+    // The next LP's data into L2 now, a refinement's time before its build.
+    if (lane == 0 && nitem < nitems && !P.shared && fits_lp(nm, nn)) warp_prefetch(P, nm, nn, na, nb, nc);
     const int64_t yoff = P.R.y_off ? P.R.y_off[lp] : boff;    // outputs packed like b, or at y_off
     int32_t *bp = P.bbuf ? P.bbuf + (P.bpacked ? yoff : int64_t(lp) * P.B.max_m) : nullptr;
     if (bp)
