@@ -708,31 +708,44 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
     float *coef = reinterpret_cast<float *>(xq + kRefK);                 // r of the p-th non-basic slack
     float *dq = coef + kRefK;                                            // dx of the q-th basic structural
     int *krl = reinterpret_cast<int *>(dq + kRefK);                      // row of A of the p-th non-basic slack
-    // Compaction four rows at a time in row order, lane p taking column p:
+    // Compaction in row order, lane p taking column p (with at most 16 columns
+    // the half-warps take alternate rows, eight rows a step, else four):
     // compacted rows up to i end before tableau row i + 1 starts (ks < S), so
     // no row is overwritten unread.
+    const bool halves = kn <= 16;             // per-column work in both half-warps
     {
-      const int c = lane < kn ? int(nsl[lane]) : 0;
+      const int p = halves ? (lane & 15) : lane, h = halves ? (lane >> 4) : 0, dr = halves ? 2 : 1;
+      const int c = p < kn ? int(nsl[p]) : 0;
 #pragma unroll 1
-      for (int i0 = 0; i0 < m; i0 += 4) {
+      for (int i0 = 0; i0 < m; i0 += 4 * dr) {
         float v[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) v[r] = (lane < kn && i0 + r < m) ? T[(i0 + r) * S + c] : 0.f;
+        for (int r = 0; r < 4; ++r) {
+          const int i = i0 + h + dr * r;
+          v[r] = (p < kn && i < m) ? T[i * S + c] : 0.f;
+        }
         __syncwarp();
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
-          if (lane < kn && i0 + r < m) tcomp[(i0 + r) * ks + lane] = v[r];
+        for (int r = 0; r < 4; ++r) {
+          const int i = i0 + h + dr * r;
+          if (p < kn && i < m) tcomp[i * ks + p] = v[r];
+        }
         __syncwarp();
       }
     }
     {
       const double *Ad = static_cast<const double *>(P.B.A) + aoff;
-      // A's basic columns row by row, lane q taking column j_q: one copy
-      // instruction per row touches only that row's lines.
-      if (lane < k) {
-        const double *src = Ad + bas[sbl[lane]];
+      // A's basic columns row by row, lane q taking column j_q (with at most 16
+      // columns the half-warps take alternate rows): one copy instruction
+      // touches only one or two rows' lines.
+      {
+        const int q = halves ? (lane & 15) : lane, h = halves ? (lane >> 4) : 0, dr = halves ? 2 : 1;
+        if (q < k) {
+          const double *src = Ad + bas[sbl[q]] + static_cast<long long>(h) * n;
+          double *dst = ac + h * ks + q;
 #pragma unroll 1
-        for (int i = 0; i < m; ++i, src += n) cp_async8(ac + i * ks + lane, src);
+          for (int i = h; i < m; i += dr, src += static_cast<long long>(dr) * n, dst += dr * ks) cp_async8(dst, src);
+        }
       }
 #pragma unroll 1
       for (int p = 0; p < kn; ++p) {
@@ -845,19 +858,26 @@ __global__ void __launch_bounds__(kWarpMaxWarps * 32, 1) warp_kernel(TableauPara
           dxs[t2] = v2 < n ? s2 : 0.f;
         }
       }
-      // dy_p = sum_t T[t, c_p] rho_t for the non-basic slacks (kn <= 32).
-      if (lane < kn) {
+      // dy_p = sum_t T[t, c_p] rho_t for the non-basic slacks (kn <= 32); with
+      // at most 16 the half-warps sum alternate rows and add their totals.
+      {
+        const int p = halves ? (lane & 15) : lane, h = halves ? (lane >> 4) : 0, dr = halves ? 2 : 1;
         float a0 = 0.f, a1 = 0.f;
-        int t = 0;
+        if (p < kn) {
+          int t = h;
 #pragma unroll 1
-        for (; t + 1 < m; t += 2) {
-          a0 = fmaf(tcomp[t * ks + lane], colb[t], a0);
-          a1 = fmaf(tcomp[(t + 1) * ks + lane], colb[t + 1], a1);
+          for (; t + dr < m; t += 2 * dr) {
+            a0 = fmaf(tcomp[t * ks + p], colb[t], a0);
+            a1 = fmaf(tcomp[(t + dr) * ks + p], colb[t + dr], a1);
+          }
+          if (t < m) a0 = fmaf(tcomp[t * ks + p], colb[t], a0);
         }
-        if (t < m) a0 = fmaf(tcomp[t * ks + lane], colb[t], a0);
-        const float dy = a0 + a1;
-        yqs[lane] += f2d_exact(dy);
-        coef[lane] = dy;                       // dy of the p-th non-basic slack, for the certificate
+        float dy = a0 + a1;
+        if (halves) dy += __shfl_xor_sync(kFull, dy, 16);
+        if (lane < kn) {
+          yqs[lane] += f2d_exact(dy);
+          coef[lane] = dy;                     // dy of the p-th non-basic slack, for the certificate
+        }
       }
       __syncwarp();
       if (lane < k) dq[lane] = dxs[sbl[lane]];
